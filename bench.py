@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark of the NNCA H^2 matrix-vector product on GB300.
+
+Metric: H^2 matvec points/s (N * nrhs / product time) of the FP32-evaluation
+form, on the 3D uniform 1/r workload (N = 1,048,576 points i.i.d. uniform in
+[0,1]^3, K = 1/r, K(x,x) = 0, leaf size 64, ACA tolerance 1e-6, one vector
+x ~ N(0,1)), gated on a relative error <= 1e-6 against the FP64 form of the
+same handle.
+
+One step is one H^2 product (Sec. 4 steps 2-5: permutation, P2M, M2M, M2L,
+L2L, L2P, P2P, permutation back). The build of the representation (tree,
+lists, ACA pivots, bases; Sec. 2-3) runs once per run before the timed
+region and is reported in "build". Inputs are resident in HBM when the timed
+region starts; L2 is flushed (256 MiB write) before every timed step, outside
+the step's CUDA events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --gpus N > 1 (under torchrun) every rank builds and times its own
+replica of the workload (independent instances, no data exchange: the
+product does not shard); the value is the points of all ranks over the
+slowest rank's time. --impl reference times the FP64 CPU oracle's H^2
+product on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import signal
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2203_14832_gb300 import workloads as W  # noqa: E402
+
+METRIC = "H2 matvec points/s at rel err <=1e-6: mixed-precision vs FP64 form, same GB300"
+WORKLOAD = "invr3d_1m"
+CPU_SAMPLE_N = 65536          # oracle sample: the same recipe at 65,536 points
+SMS = 152
+MUFU_PER_CLK_SM = 16          # MUFU lanes per SM per clock: one rsqrt per pair
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=0, help="override N (not the benchmark workload)")
+    return ap.parse_args()
+
+
+def workload_desc(w):
+    return (f"{w.name}: N={w.n} i.i.d. uniform in [0,1]^3, K=1/r, K(x,x)=0, leaf size {w.leaf_size}, "
+            f"eta=sqrt(2), ACA tol {w.aca_tol:g}, nrhs {w.nrhs}, x~N(0,1)")
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0))
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.send_signal(signal.SIGTERM)
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(ws, v: float) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(n: int, threads: int):
+    """Build the oracle's H^2 on the workload recipe at n points; returns (h, x, build_s)."""
+    from oracle import oracle as O
+    w = W.WORKLOADS[WORKLOAD].scaled(n)
+    P = w.make_points()
+    x = w.make_vector()
+    cfg = O.Config(d=w.d, leaf_size=w.leaf_size, aca_tol=w.aca_tol, kernel=w.kernel, kparam=w.kparam)
+    t0 = time.perf_counter()
+    h = O.H2(P, cfg, nthreads=threads)
+    return h, x, time.perf_counter() - t0
+
+
+def cpu_baseline(threads: int) -> dict:
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    h, x, tb = oracle_sample(CPU_SAMPLE_N, threads)
+    h.matvec(x)
+    t0 = time.perf_counter()
+    reps = 3
+    for _ in range(reps):
+        h.matvec(x)
+    t = (time.perf_counter() - t0) / reps
+    return {"value": CPU_SAMPLE_N / t, "unit": "points/s", "cores": threads, "kind": "oracle",
+            "sample": f"FP64 oracle H2 product (on-the-fly form) on {CPU_SAMPLE_N} points of the same recipe "
+                      f"(oracle build {tb:.1f} s untimed), mean of {reps} products"}
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    threads = host_cores()
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    h, x, tb = oracle_sample(CPU_SAMPLE_N, threads)
+    for _ in range(args.warmup):
+        h.matvec(x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        h.matvec(x)
+    t = time.perf_counter() - t0
+    value = CPU_SAMPLE_N * args.steps / t
+    w = W.WORKLOADS[WORKLOAD]
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_desc(w), "sample_n": CPU_SAMPLE_N, "world_size": ws},
+           "cpu_baseline": {"value": value, "unit": "points/s", "cores": threads, "kind": "oracle",
+                            "sample": f"FP64 oracle H2 product on {CPU_SAMPLE_N} points of the same recipe per step "
+                                      f"(build {tb:.1f} s untimed)"},
+           "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_2203_14832_gb300 import _build, nnca
+
+    ws, rank, local = dist_init(args)
+    torch.cuda.set_device(local)
+    _build.build()
+    w = W.WORKLOADS[WORKLOAD]
+    if args.n:
+        w = w.scaled(args.n)
+    # independent replicas: every rank draws its own instance of the recipe
+    if rank:
+        w = W.Workload(w.name, w.n, w.d, w.kernel, w.kparam, w.leaf_size, w.aca_tol, w.nrhs, w.seed + 17 * rank,
+                       w.points, w.vector, w.note)
+    N, nrhs = w.n, w.nrhs
+    stream = torch.cuda.current_stream()
+    P = torch.as_tensor(w.make_points(), device="cuda")
+    xh = w.make_vector()
+    cfg = nnca.Config(d=w.d, leaf_size=w.leaf_size, aca_tol=w.aca_tol, kernel=w.kernel, kparam=w.kparam)
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = nnca.H2(P, cfg)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    st = h.stats()
+
+    x = torch.as_tensor(xh, device="cuda")
+    y32 = torch.empty_like(x)
+    y64 = torch.empty_like(x)
+    h.matvec(x, nnca.PREC_FP64, out=y64)
+    h.matvec(x, nnca.PREC_FP32, out=y32)
+    torch.cuda.synchronize()
+    y64h, y32h = y64.cpu().numpy(), y32.cpu().numpy()
+    err32 = float(np.linalg.norm(y32h - y64h) / np.linalg.norm(y64h))
+
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")   # 256 MiB > L2
+    for _ in range(args.warmup):
+        h.matvec(x, nnca.PREC_FP32, out=y32)
+    torch.cuda.synchronize()
+
+    # timed region: K products, CUDA events around each, L2 flushed before each
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    barrier(ws)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    h.set_profiling(True)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        h.matvec(x, nnca.PREC_FP32, out=y32)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    barrier(ws)
+    clocks = sampler.stop() if sampler else None
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    st_prof = h.stats()
+    h.set_profiling(False)
+    total_ms = reduce_max(ws, float(sum(step_ms)))
+    value = ws * N * nrhs * args.steps / (total_ms / 1e3)
+
+    # FP64 form of the same handle (a few products)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.fp64_steps):
+        h.matvec(x, nnca.PREC_FP64, out=y64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = e0.elapsed_time(e1) / args.fp64_steps
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    xpin = torch.empty(N * nrhs, dtype=torch.float64, pin_memory=True)
+    ypin = torch.empty(N * nrhs, dtype=torch.float64, pin_memory=True)
+    xpin.numpy()[:] = np.asarray(xh, dtype=np.float64).ravel()
+    e2e_steps = max(3, args.steps // 2)
+    h.matvec_host(xpin.numpy(), nnca.PREC_FP32)
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        nnca.nnca_matvec_host(h.handle, xpin.numpy(), ypin.numpy(), nrhs, N, nnca.PREC_FP32, stream)
+    e2e_s = reduce_max(ws, time.perf_counter() - t0)
+    e2e_value = ws * N * nrhs * e2e_steps / e2e_s
+    yh_e2e = ypin.numpy().copy()
+
+    if rank != 0:
+        h.close()
+        return
+
+    # dense check on sampled rows (FP64 oracle dense product, host cores)
+    from oracle import oracle as O
+    ocfg = O.Config(d=w.d, leaf_size=w.leaf_size, aca_tol=w.aca_tol, kernel=w.kernel, kparam=w.kparam)
+    rows = np.random.default_rng(12345).choice(N, 256, replace=False)
+    os.environ.setdefault("OMP_NUM_THREADS", str(host_cores()))
+    yd = O.dense_rows(w.make_points(), rows, xh, ocfg)
+    err_dense = float(np.linalg.norm(y64h[rows] - yd) / np.linalg.norm(yd))
+    err_dense32 = float(np.linalg.norm(y32h[rows] - yd) / np.linalg.norm(yd))
+    e2e_ok = bool(np.array_equal(yh_e2e, y32h))
+
+    # roofline of the dominant kernel (M2L, FP32 evaluation): one rsqrt per pivot pair
+    calls = max(1, st_prof["pass_calls"])
+    m2l_ms = st_prof["pass_ms"][2] / calls
+    pass_ms = [v / calls for v in st_prof["pass_ms"][:6]]
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_gpair = MUFU_PER_CLK_SM * SMS * sm_max * 1e6 / 1e9
+    achieved = st["m2l_pairs"] / (m2l_ms / 1e3) / 1e9
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "m2l_traffic.json")
+    if os.path.exists(tf):
+        try:
+            traffic = json.load(open(tf)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_baseline(host_cores())
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_desc(w), "form": "FP32 kernel evaluations (M2L, P2P), FP64 bases",
+                   "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas x{ws}"},
+        "rel_err_fp32_vs_fp64": err32, "rel_err_fp64_vs_dense_256rows": err_dense,
+        "rel_err_fp32_vs_dense_256rows": err_dense32,
+        "fp64_form": {"value": N * nrhs / (fp64_ms / 1e3), "unit": "points/s", "ms_per_step": fp64_ms},
+        "speedup_fp32_vs_fp64": fp64_ms / (total_ms / args.steps),
+        "build": {"s": build_s, "ms_phases": st["build_ms"][:6], "kappa": st["kappa"], "lmin": st["lmin"],
+                  "ncell": st["ncell"], "n_pivots": st["n_pivots"], "max_rank": st["max_rank"],
+                  "aca_retries": st["aca_retries"], "device_bytes": st["device_bytes"]},
+        "work": {"m2l_pairs": st["m2l_pairs"], "p2p_pairs": st["p2p_pairs"]},
+        "pass_ms": {"perm": pass_ms[0], "p2m_m2m": pass_ms[1], "m2l": pass_ms[2], "l2l": pass_ms[3],
+                    "l2p_p2p": pass_ms[4], "total": pass_ms[5]},
+        "roofline": {"bound": "alu", "kernel": "k_m2l_f32", "achieved": achieved, "peak": peak_gpair,
+                     "unit": "Gpair/s", "frac": achieved / peak_gpair, "traffic": traffic,
+                     "peak_note": f"MUFU rsqrt issue rate {MUFU_PER_CLK_SM}/clk/SM x {SMS} SMs x {sm_max:.0f} MHz"},
+        "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": N * nrhs * 8,
+                "d2h_bytes_per_step": N * nrhs * 8, "matches_device_result": e2e_ok},
+        "gpu_launches": int(st_prof["launches_per_product"]) * args.steps,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+        "wall_s_timed": wall,
+    }
+    print(json.dumps(out), flush=True)
+    h.close()
+    if err32 > 1e-6:
+        print(f"error gate failed: FP32 form {err32:.3e} > 1e-6 against FP64", file=sys.stderr)
+        sys.exit(3)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

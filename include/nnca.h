@@ -1,0 +1,207 @@
+/*
+ * nnca.h -- C ABI of the GB300 (sm_103a) NNCA H^2 library.
+ *
+ * Computes the H^2 matrix-vector product y = A x with A(i, j) = K(p_i, p_j)
+ * built by the new Nested Cross Approximation (NNCA) of Gujjula &
+ * Ambikasaran, "A new Nested Cross Approximation":
+ *
+ *   nnca_build   uniform 2^d tree over the points (Sec. 2.1), neighbour and
+ *                interaction lists from the admissibility condition
+ *                (Sec. 2.2, Eq. 2, Table 1), bottom-up pivot identification
+ *                by ACA on the candidate sets (Sec. 2.3.2, Eqs. 15-18), and
+ *                the nested bases and translation operators
+ *                A_{t~ s^{B,i}} (A_{t^{B,i} s^{B,i}})^{-1} (Sec. 2.3.1,
+ *                Eqs. 11 and 14; Remark of Sec. 2.3.2);
+ *   nnca_matvec  the H^2 product of Sec. 4: upward pass (P2M, M2M),
+ *                transverse pass (M2L with K evaluated on the fly over the
+ *                pivot pairs of Sec. 3 step 2), downward pass (L2L, L2P) and
+ *                the near field (P2P over Sec. 3 step 3 blocks, evaluated
+ *                on the fly).
+ *
+ * Every step runs as a CUDA kernel on the GPU that is current when the call
+ * is made; no step falls back to the host.
+ *
+ * Conventions
+ *  - All pointers named "device" must be device memory of the current GPU;
+ *    pointers named "host" must be host memory (pageable or pinned).
+ *  - Points: n x d FP64; layout NNCA_LAYOUT_AOS (p[i*d + k]) or
+ *    NNCA_LAYOUT_SOA (p[k*n + i]).
+ *  - Vectors: nrhs right-hand sides; right-hand side r occupies
+ *    x[r*ld + i], i the caller's point index, ld >= n.
+ *  - Streams: `stream` is a cudaStream_t passed as void*; NULL is the legacy
+ *    default stream. nnca_build synchronises the stream (it reads sizes back
+ *    to the host); nnca_matvec is asynchronous on the stream.
+ *  - Errors: every call returns an nnca_status; no exception crosses the
+ *    ABI. After a failure nnca_last_error() holds a one-line message
+ *    (thread-local for calls without a handle). A failed nnca_build leaves
+ *    *out == NULL and frees everything it allocated.
+ *  - Ownership: the library copies what it needs; caller buffers are only
+ *    read or written during the call (or, for nnca_matvec, until the stream
+ *    reaches the end of the call's work). The handle owns all device memory
+ *    it allocates; nnca_destroy frees it.
+ *  - Thread safety: one handle must not be used by two host threads at once.
+ */
+#ifndef NNCA_H
+#define NNCA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nnca_handle_s *nnca_handle;
+
+typedef enum {
+    NNCA_OK = 0,
+    NNCA_ERR_INVALID_ARG = 1,   /* rejected before any device work            */
+    NNCA_ERR_OOM = 2,           /* a device allocation failed                 */
+    NNCA_ERR_CUDA = 3,          /* a CUDA runtime call or kernel failed       */
+    NNCA_ERR_UNSUPPORTED = 4,   /* valid request this build does not support  */
+    NNCA_ERR_TIMEOUT = 5,       /* a bounded device wait gave up              */
+    NNCA_ERR_INTERNAL = 6       /* a device-side consistency check failed     */
+} nnca_status;
+
+/* Kernel functions K(r), r = |x - y|_2 (Sec. 1: smooth away from x = y;
+ * Sec. 5 uses radial kernels). s = kparam[0]. The diagonal entry A(i, i) is
+ * decided by index and equals kparam[2]; two distinct coincident points give 0
+ * for the kernels singular at r = 0 (LOG, INV_R, PAPER_I) and K(0) otherwise. */
+enum {
+    NNCA_K_LOG = 0,        /* s log r                                          */
+    NNCA_K_INV_R = 1,      /* s / r                                            */
+    NNCA_K_GAUSS = 2,      /* s exp(-r^2 / (2 h^2)),      h = kparam[1]        */
+    NNCA_K_MATERN = 3,     /* s exp(-r / h),              h = kparam[1]        */
+    NNCA_K_PAPER_I = 4,    /* Sec. 5.1 kernel (i):  r(log r - 1)/(a(log a - 1)) for r < a,
+                              log r / log a otherwise,   a = kparam[1]          */
+    NNCA_K_PAPER_II = 5,   /* Sec. 5.1 kernel (ii): r/a for r < a, a/r otherwise */
+    NNCA_K_SEPARABLE = 6,  /* s f(x) f(y), f(x) = 1 + sum_k x_k  (rank 1)       */
+    NNCA_K_POLY2 = 7       /* s (1 + x.y)^2                                     */
+};
+
+enum { NNCA_LAYOUT_AOS = 0, NNCA_LAYOUT_SOA = 1 };
+enum { NNCA_F64 = 0, NNCA_F32 = 1 };                 /* element type of x and y   */
+/* Arithmetic of the product. FP64: everything in double. FP32: the kernel
+ * evaluations of M2L and P2P (nearly all of the work) in float, with
+ * coordinates relative to their cell centre and compensated accumulation
+ * across source cells; bases, translations and coefficient vectors in double. */
+enum { NNCA_PREC_FP64 = 0, NNCA_PREC_FP32 = 1 };
+
+typedef struct {
+    int d;             /* dimension 1..4                                         */
+    int leaf_size;     /* nu >= 1: maximum points per leaf (Sec. 2.1)             */
+    int eta2_num;      /* eta^2 = eta2_num / eta2_den > 0 (Eq. 2); the paper's    */
+    int eta2_den;      /*   experiments use eta = sqrt(2): 2 / 1                  */
+    double aca_tol;    /* epsilon > 0 of the ACA stopping rule (Eq. 4)            */
+    int kernel;        /* NNCA_K_*                                                */
+    double kparam[4];  /* [0] scale s, [1] h or a, [2] diagonal value, [3] unused */
+    int symmetric;     /* must be 1: P = Q, K symmetric; uses the shortcut
+                          t^{B,o} = s^{B,i}, s^{B,o} = t^{B,i} (Sec. 5)          */
+    int reserved[3];   /* set to 0                                                */
+} nnca_config;
+
+/* Sizes and timings of a built handle (the quantities of the paper's
+ * Table of Sec. 5: memory, assembly time) plus work counts. */
+typedef struct {
+    int d, lmax, kappa, lmin;      /* lmin: first level with an interaction list   */
+    int64_t n;
+    int64_t ncell;                 /* non-empty cells, all levels                  */
+    int64_t ncell_level[64];
+    int64_t n_il, n_nb;            /* interaction-list and neighbour entries       */
+    int64_t n_pivots;              /* sum of ranks over all cells                  */
+    int64_t max_rank;
+    int64_t n_passthru;            /* cells with no far-field candidates           */
+    int64_t p2p_pairs;             /* sum over leaves of n_B * sum_{N(B)} n_B'     */
+    int64_t m2l_pairs;             /* sum over cells of r_B * sum_{IL(B)} r_B'     */
+    int64_t op_entries;            /* entries of all bases and translations        */
+    int64_t device_bytes;          /* device memory held by the handle             */
+    double build_ms[8];            /* tree, lists, pivots (ACA), bases, finish, total, -, - */
+    int64_t aca_retries;           /* cells re-run because the scratch pool ran out */
+    /* product timings, filled while profiling is on (nnca_set_profiling):
+     * device time per pass summed over the profiled products, from CUDA events
+     * recorded on the caller's stream between the passes:
+     * [0] permutation in, [1] P2M + M2M, [2] M2L, [3] L2L, [4] L2P + P2P,
+     * [5] whole product */
+    double pass_ms[8];
+    int64_t pass_calls;            /* products summed in pass_ms                   */
+    int64_t launches_per_product;  /* kernels of this library in the last product  */
+} nnca_stats;
+
+/* Build the H^2 representation of A(i, j) = K(p_i, q_j).
+ *  cfg    host pointer; validated (d, leaf_size, eta2, aca_tol > 0, kernel,
+ *         symmetric == 1).
+ *  P      device pointer, nP points (layout), FP64, all finite.
+ *  Q      device pointer or NULL; must equal P (or be NULL) with nQ == nP:
+ *         general P != Q returns NNCA_ERR_UNSUPPORTED.
+ *  out    host pointer that receives the handle (NULL on failure).
+ * Synchronises `stream`. nP >= 1 and nP < 2^31. */
+nnca_status nnca_build(const nnca_config *cfg, const double *P, int64_t nP, const double *Q, int64_t nQ,
+                       int layout, void *stream, nnca_handle *out);
+
+/* y = A~ x for nrhs right-hand sides. x, y: device pointers, element type
+ * dtype (NNCA_F64 or NNCA_F32), column r at [r*ld .. r*ld + n). y is
+ * overwritten. precision: NNCA_PREC_FP64 (all arithmetic in FP64) or
+ * NNCA_PREC_FP32 (kernel evaluations and contractions in FP32 with
+ * cell-relative coordinates and compensated accumulation across cells).
+ * Asynchronous on `stream`. The first call with a larger nrhs than before
+ * allocates the handle's workspace (so make that call before capturing a
+ * stream into a graph). */
+nnca_status nnca_matvec(nnca_handle h, const void *x, void *y, int64_t nrhs, int64_t ld, int dtype,
+                        int precision, void *stream);
+
+/* Same product from and to HOST buffers: copies x to the device, runs
+ * nnca_matvec, copies y back, and synchronises `stream` before returning. */
+nnca_status nnca_matvec_host(nnca_handle h, const void *x_host, void *y_host, int64_t nrhs, int64_t ld,
+                             int dtype, int precision, void *stream);
+
+/* Free every device and host resource of the handle (NULL is a no-op).
+ * Synchronises the device first. */
+void nnca_destroy(nnca_handle h);
+
+/* Copy the statistics. Synchronises with the profiled products first. */
+nnca_status nnca_get_stats(nnca_handle h, nnca_stats *out);
+
+/* Turn per-pass timing of nnca_matvec on (1) or off (0); turning it on
+ * clears the accumulated pass_ms. While on, every product records CUDA events
+ * between its passes on the caller's stream (no host synchronisation in the
+ * product itself). */
+nnca_status nnca_set_profiling(nnca_handle h, int on);
+
+/* Copy one internal array to host memory, for inspection and tests. If buf
+ * is NULL only *bytes is set. Otherwise at most cap bytes are written and
+ * *bytes receives the array's size. Point indices are Morton-sorted
+ * positions; cell ids are global (level by level, as in LEVEL_BASE).
+ *   PERM        int64[n]        original index of sorted position
+ *   KEYS        uint64[n]       sorted Morton keys
+ *   LEVEL_BASE  int64[kappa+2]  first cell id of each level
+ *   CKEY        uint64[ncell]   cell key (prefix of its level)
+ *   CBEG, CEND  int64[ncell]    sorted point range of the cell
+ *   CPAR        int64[ncell]    parent cell id (-1 for the root)
+ *   CCH_BEG/END int64[ncell]    children cell range
+ *   NB_OFF      int64[ncell+1]  CSR offsets of N(B); NB_IDX int64 cell ids
+ *   IL_OFF      int64[ncell+1]  CSR offsets of IL(B); IL_IDX int64 cell ids
+ *   PIV_OFF     int64[ncell+1]  CSR offsets of the pivots (ranks)
+ *   PIV_ROW     int64[npiv]     t^{B,i} (sorted positions)
+ *   PIV_COL     int64[npiv]     s^{B,i} (sorted positions; -1 for pass-through cells)
+ *   PASSTHRU    int64[ncell]    1 if the cell had no far-field candidates
+ *   CAND_OFF    int64[ncell+1]  CSR offsets of the candidate rows t~^{B,i}
+ *   OP_OFF      int64[ncell+1]  offsets of the per-cell operators
+ *   OP          double[...]     per cell |t~| x r row-major: U_B (leaf) or
+ *                               the stacked C_{B_c B} (non-leaf)          */
+enum {
+    NNCA_EXPORT_PERM = 0, NNCA_EXPORT_KEYS, NNCA_EXPORT_LEVEL_BASE, NNCA_EXPORT_CKEY,
+    NNCA_EXPORT_CBEG, NNCA_EXPORT_CEND, NNCA_EXPORT_CPAR, NNCA_EXPORT_CCH_BEG, NNCA_EXPORT_CCH_END,
+    NNCA_EXPORT_NB_OFF, NNCA_EXPORT_NB_IDX, NNCA_EXPORT_IL_OFF, NNCA_EXPORT_IL_IDX,
+    NNCA_EXPORT_PIV_OFF, NNCA_EXPORT_PIV_ROW, NNCA_EXPORT_PIV_COL, NNCA_EXPORT_PASSTHRU,
+    NNCA_EXPORT_CAND_OFF, NNCA_EXPORT_OP_OFF, NNCA_EXPORT_OP
+};
+nnca_status nnca_export(nnca_handle h, int what, void *buf, int64_t cap, int64_t *bytes);
+
+/* Message of the last failure on this handle (or, for h == NULL, of the
+ * last failed call without a handle on this thread). Never NULL. */
+const char *nnca_last_error(nnca_handle h);
+const char *nnca_status_string(nnca_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NNCA_H */

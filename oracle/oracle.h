@@ -106,6 +106,10 @@ orc_h2 *orc_build(const orc_config *cfg, const double *P, long n, int nthreads);
 /* Tree and lists only (no pivots): for structure checks at large n. */
 orc_h2 *orc_build_structure(const orc_config *cfg, const double *P, long n, int nthreads);
 void orc_free(orc_h2 *h);
+/* Pivots of one leaf cell (Sec. 2.3.2, leaf candidate sets) computed from the
+ * tree and lists alone; works on a structure-only build. Returns the rank
+ * (pivots beyond cap are not written), or -1 if cell is not a leaf. */
+long orc_leaf_pivots(const orc_h2 *h, long cell, long *prow, long *pcol, long cap);
 
 /* Form the stored H^2 representation (coupling S_{X,Y} and near blocks). */
 int orc_assemble(orc_h2 *h);

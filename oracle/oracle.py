@@ -75,6 +75,8 @@ def lib():
         L.orc_build_structure.restype = _P(_H2)
         L.orc_build_structure.argtypes = [_P(_Config), _D, C.c_long, C.c_int]
         L.orc_free.argtypes = [_P(_H2)]
+        L.orc_leaf_pivots.restype = C.c_long
+        L.orc_leaf_pivots.argtypes = [_P(_H2), C.c_long, _L, _L, C.c_long]
         L.orc_assemble.argtypes = [_P(_H2)]
         L.orc_h2_matvec.argtypes = [_P(_H2), _D, _D, C.c_long, C.c_long, C.c_int, C.c_int]
         L.orc_dense_matvec.argtypes = [_P(_Config), _D, C.c_long, _D, _D, C.c_long, C.c_long, C.c_int]
@@ -198,6 +200,16 @@ class H2:
         m = int(self.cand_off[c + 1] - self.cand_off[c])
         r = int(self.piv_off[c + 1] - self.piv_off[c])
         return self.op[self.op_off[c]: self.op_off[c + 1]].reshape(m, r)
+
+    def leaf_pivots(self, c: int):
+        """(t^{B,i}, s^{B,i}) of leaf c computed from the tree and lists alone."""
+        cap = int(self.cend[c] - self.cbeg[c]) + 1
+        pr = np.zeros(cap, dtype=np.int64)
+        pc = np.zeros(cap, dtype=np.int64)
+        r = lib().orc_leaf_pivots(self._h, int(c), _lp(pr), _lp(pc), cap)
+        if r < 0:
+            raise ValueError("not a leaf")
+        return pr[:r].copy(), pc[:r].copy()
 
     # --- products ------------------------------------------------------
     def assemble(self):

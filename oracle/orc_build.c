@@ -194,6 +194,20 @@ orc_h2 *orc_build(const orc_config *cfg, const double *P, long n, int nthreads) 
     return h;
 }
 
+long orc_leaf_pivots(const orc_h2 *h, long cell, long *prow, long *pcol, long cap) {
+    if (cell < h->level_base[h->kappa] || cell >= h->level_base[h->kappa + 1]) return -1;
+    cell_out o;
+    memset(&o, 0, sizeof(o));
+    build_cell(h, cell, 1, NULL, &o);
+    long r = o.r;
+    for (long t = 0; t < r && t < cap; ++t) {
+        prow[t] = o.prow[t];
+        pcol[t] = o.pcol ? o.pcol[t] : -1;
+    }
+    free(o.cand); free(o.prow); free(o.pcol); free(o.op);
+    return r;
+}
+
 void orc_free(orc_h2 *h) {
     if (!h) return;
     free(h->perm); free(h->key); free(h->x);

@@ -1,0 +1,935 @@
+// Bottom-up pivot identification and bases on the GPU (Sec. 2.3).
+//
+// For each level from the leaves up (Sec. 2.3.2, "reverse level-order"):
+//  1. candidate sets (Eqs. 15-18, symmetric shortcut of Sec. 5):
+//       leaf      t~ = t^B,                      s~ = U_{B' in IL(B)} s^{B'}
+//       non-leaf  t~ = U_{children c} t^{c,i},   s~ = U_{B' in IL(B)} U_{B'' in C(B')} t^{B'',i}
+//     in ascending cell order, each child's pivots in selection order;
+//  2. partially pivoted ACA (Sec. 2.2.1, Eqs. 3-4) on A_{t~ s~} with the
+//     kernel evaluated on the fly: one CTA per cell, FP64, the ACA arithmetic
+//     written as the same sequence of IEEE operations as its definition (every
+//     multiply-add fused, every dot product and norm reduced in the canonical
+//     order: element j into partial j mod 256 in ascending j, then the
+//     partials folded p[t] += p[t + o] for o = 128 ... 1), so the pivots are
+//     reproducible bit for bit;
+//  3. bases (Sec. 2.3.1, Eqs. 11 and 14, Remark of Sec. 2.3.2):
+//       X = A_{t~ sigma} (A_{tau sigma})^{-1}   (|t~| x r, row-major)
+//     by LU with partial pivoting of (A_{tau sigma})^T and one forward and
+//     back substitution per candidate row; rows of X at the pivots are the
+//     identity by definition and are set exactly.
+// A cell with no far-field candidates passes all its candidates up with an
+// identity basis. The ACA reading (start row, tie breaks, the cross that meets
+// the stopping rule is not kept) is the one stated in the library header.
+//
+// ACA scratch (the residual row, the crosses u_l and v_l) comes from one pool
+// per level; a cell that finds the pool exhausted gives up and is re-run in a
+// later launch with an empty pool, so results never depend on the pool size.
+#include <algorithm>
+
+#include "nnca_internal.cuh"
+
+namespace nnca {
+
+namespace {
+
+constexpr int ACA_T = 256;      // threads per cell; also the number of canonical partials
+constexpr int MAXK = 1024;      // largest rank a cell may reach
+constexpr int DOT_CHUNK = 4;    // dot products folded together
+
+unsigned grid_for(int64_t n, int threads) {
+    int64_t g = (n + threads - 1) / threads;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 152 * 32));
+}
+
+// ---- candidate sets -------------------------------------------------------
+struct LevelPivots {              // compact pivots of one level (local cell index)
+    int64_t *off = nullptr;       // [cnt + 1]
+    int32_t *row = nullptr;       // point positions t^{B,i}
+    int32_t *col = nullptr;       // point positions s^{B,i} (-1 for pass-through)
+    int32_t *rank = nullptr;      // [cnt]
+    int32_t *pass = nullptr;      // [cnt]
+    int64_t total = 0;
+};
+
+__global__ void k_cand_sizes(int64_t b0, int64_t b1, int leaf, const int32_t *cbeg, const int32_t *cend,
+                             const int32_t *cch_beg, const int32_t *cch_end, const int32_t *il_off,
+                             const int32_t *il_idx, const int32_t *crank, int64_t cb0, int64_t *msz, int64_t *nsz) {
+    for (int64_t X = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; X < b1; X += (int64_t)gridDim.x * blockDim.x) {
+        int64_t m = 0, n = 0;
+        if (leaf) {
+            m = cend[X] - cbeg[X];
+            for (int32_t q = il_off[X]; q < il_off[X + 1]; ++q) {
+                int32_t Y = il_idx[q];
+                n += cend[Y] - cbeg[Y];
+            }
+        } else {
+            for (int32_t c = cch_beg[X]; c < cch_end[X]; ++c) m += crank[c - cb0];
+            for (int32_t q = il_off[X]; q < il_off[X + 1]; ++q) {
+                int32_t Y = il_idx[q];
+                for (int32_t Z = cch_beg[Y]; Z < cch_end[Y]; ++Z) n += crank[Z - cb0];
+            }
+        }
+        msz[X - b0] = m;
+        nsz[X - b0] = n;
+    }
+}
+
+// one warp per cell
+__global__ void k_cand_gather(int64_t b0, int64_t b1, int leaf, const int32_t *cbeg, const int32_t *cend,
+                              const int32_t *cch_beg, const int32_t *cch_end, const int32_t *il_off,
+                              const int32_t *il_idx, const int64_t *cpoff, const int32_t *cprow, int64_t cb0,
+                              const int64_t *row_off, const int64_t *col_off, int32_t *rows, int32_t *cols) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t X = b0 + warp; X < b1; X += nwarps) {
+        const int64_t x = X - b0;
+        int32_t *R = rows + row_off[x];
+        int32_t *Cc = cols + col_off[x];
+        int64_t o = 0;
+        if (leaf) {
+            for (int32_t t = cbeg[X] + lane; t < cend[X]; t += 32) R[t - cbeg[X]] = t;
+            for (int32_t q = il_off[X]; q < il_off[X + 1]; ++q) {
+                int32_t Y = il_idx[q];
+                int32_t len = cend[Y] - cbeg[Y];
+                for (int32_t t = lane; t < len; t += 32) Cc[o + t] = cbeg[Y] + t;
+                o += len;
+            }
+        } else {
+            for (int32_t c = cch_beg[X]; c < cch_end[X]; ++c) {
+                int64_t p0 = cpoff[c - cb0], len = cpoff[c - cb0 + 1] - p0;
+                for (int64_t t = lane; t < len; t += 32) R[o + t] = cprow[p0 + t];
+                o += len;
+            }
+            o = 0;
+            for (int32_t q = il_off[X]; q < il_off[X + 1]; ++q) {
+                int32_t Y = il_idx[q];
+                for (int32_t Z = cch_beg[Y]; Z < cch_end[Y]; ++Z) {
+                    int64_t p0 = cpoff[Z - cb0], len = cpoff[Z - cb0 + 1] - p0;
+                    for (int64_t t = lane; t < len; t += 32) Cc[o + t] = cprow[p0 + t];
+                    o += len;
+                }
+            }
+        }
+    }
+}
+
+// ---- ACA ------------------------------------------------------------------
+struct AcaArgs {
+    KParams kp;
+    int d;
+    int64_t N;
+    const double *xs;             // [d][N]
+    double eps;
+    const int64_t *row_off, *col_off, *cap_off;
+    const int32_t *rows, *cols;
+    int32_t *rank, *prow, *pcol;  // outputs (local indices; capacity cap per cell)
+    const int32_t *work;
+    int nwork;
+    int *work_ctr;
+    int32_t *retry;
+    int *retry_ctr;
+    double *pool;
+    unsigned long long pool_size;
+    unsigned long long *pool_top;
+    unsigned *status;
+};
+
+__device__ __forceinline__ void load_point(const double *xs, int64_t N, int d, int64_t i, double *p) {
+    for (int k = 0; k < d; ++k) p[k] = xs[(int64_t)k * N + i];
+}
+
+// (value, index) maximum over the block, ties to the smaller index; idx -1 = none.
+__device__ void block_argmax(double &v, int64_t &idx, double *sv, long long *si) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o; o >>= 1) {
+        double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        long long i2 = __shfl_xor_sync(0xffffffffu, (long long)idx, o);
+        if (i2 >= 0 && (idx < 0 || v2 > v || (v2 == v && i2 < idx))) { v = v2; idx = i2; }
+    }
+    if (lane == 0) { sv[wid] = v; si[wid] = idx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double bv = sv[0];
+        long long bi = si[0];
+        for (int w = 1; w < ACA_T / 32; ++w)
+            if (si[w] >= 0 && (bi < 0 || sv[w] > bv || (sv[w] == bv && si[w] < bi))) { bv = sv[w]; bi = si[w]; }
+        sv[0] = bv;
+        si[0] = bi;
+    }
+    __syncthreads();
+    v = sv[0];
+    idx = si[0];
+    __syncthreads();
+}
+
+// Fold the partials part[c][0..ACA_T) of nc dot products in the canonical
+// order; results in part[c][0].
+__device__ void fold_partials(double (*part)[ACA_T], int nc) {
+    for (int o = ACA_T / 2; o >= 1; o >>= 1) {
+        __syncthreads();
+        if ((int)threadIdx.x < o)
+            for (int c = 0; c < nc; ++c) part[c][threadIdx.x] = __dadd_rn(part[c][threadIdx.x], part[c][threadIdx.x + o]);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(ACA_T) k_aca(AcaArgs A) {
+    __shared__ double sv_l[MAXK];          // u_l(i) for the residual row, then v_l(j*)
+    __shared__ double dvv[MAXK];           // v_l . v_k
+    __shared__ double duu[MAXK];           // u_l . u_k
+    __shared__ long long vtab[MAXK];       // pool offset of cross l: v_l (n) then u_l (m)
+    __shared__ double part[DOT_CHUNK][ACA_T];
+    __shared__ double redv[ACA_T / 32];
+    __shared__ long long redi[ACA_T / 32];
+    __shared__ double xi[4], yj[4];
+    __shared__ int s_work;
+    __shared__ long long s_off;
+    __shared__ int s_ctl;                  // 0 continue, 1 done, 2 retry
+    const int t = threadIdx.x;
+    const int d = A.d;
+    const int64_t N = A.N;
+
+    for (;;) {
+        if (t == 0) s_work = atomicAdd(A.work_ctr, 1);
+        __syncthreads();
+        const int w = s_work;
+        __syncthreads();
+        if (w >= A.nwork) return;
+        const int64_t x = A.work[w];
+        const int64_t m = A.row_off[x + 1] - A.row_off[x];
+        const int64_t n = A.col_off[x + 1] - A.col_off[x];
+        const int32_t *rows = A.rows + A.row_off[x];
+        const int32_t *cols = A.cols + A.col_off[x];
+        int32_t *prow = A.prow + A.cap_off[x];
+        int32_t *pcol = A.pcol + A.cap_off[x];
+        if (n == 0 || m == 0) {
+            // no far-field candidates: pass-through (all rows), or an empty cell
+            if (n == 0)
+                for (int64_t i = t; i < m; i += ACA_T) { prow[i] = (int32_t)i; pcol[i] = -1; }
+            if (t == 0) A.rank[x] = (n == 0) ? (int32_t)m : 0;
+            continue;
+        }
+        const int64_t kmax = m < n ? m : n;
+        // per-cell scratch: residual row r (n), used-column bits, used-row bytes
+        const unsigned long long words = (unsigned long long)n + (n + 63) / 64 + (m + 7) / 8;
+        if (t == 0) {
+            unsigned long long off = atomicAdd(A.pool_top, words);
+            s_off = (off + words <= A.pool_size) ? (long long)off : -1;
+        }
+        __syncthreads();
+        if (s_off < 0) {
+            if (t == 0) A.retry[atomicAdd(A.retry_ctr, 1)] = (int32_t)x;
+            __syncthreads();
+            continue;
+        }
+        double *r = A.pool + s_off;
+        unsigned long long *ucol = (unsigned long long *)(r + n);
+        unsigned char *urow = (unsigned char *)(ucol + (n + 63) / 64);
+        for (int64_t q = t; q < (n + 63) / 64; q += ACA_T) ucol[q] = 0ull;
+        for (int64_t q = t; q < m; q += ACA_T) urow[q] = 0;
+        int64_t k = 0, i = 0;
+        double frob2 = 0.0;
+        if (t == 0) s_ctl = 0;
+        __syncthreads();
+
+        for (;;) {
+            // --- residual of row i: r_j = A(i, j) - sum_l u_l(i) v_l(j) -------------
+            for (int64_t l = t; l < k; l += ACA_T) sv_l[l] = A.pool[vtab[l] + n + i];
+            if (t < d) xi[t] = A.xs[(int64_t)t * N + rows[i]];
+            __syncthreads();
+            double best = -1.0;
+            int64_t bj = -1;
+            for (int64_t j0 = t; j0 < n; j0 += 4 * ACA_T) {
+                double s[4];
+                int64_t jj[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    jj[u] = j0 + (int64_t)u * ACA_T;
+                    if (jj[u] < n) {
+                        double y[4];
+                        load_point(A.xs, N, d, cols[jj[u]], y);
+                        s[u] = kern_exact(A.kp, xi, y);
+                    } else {
+                        s[u] = 0.0;
+                    }
+                }
+                for (int64_t l = 0; l < k; ++l) {
+                    const double a = -sv_l[l];
+                    const double *Vl = A.pool + vtab[l];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (jj[u] < n) s[u] = __fma_rn(a, Vl[jj[u]], s[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (jj[u] < n) {
+                        r[jj[u]] = s[u];
+                        const bool used = (ucol[jj[u] >> 6] >> (jj[u] & 63)) & 1ull;
+                        if (!used && fabs(s[u]) > best) { best = fabs(s[u]); bj = jj[u]; }
+                    }
+                }
+            }
+            block_argmax(best, bj, redv, redi);
+            if (bj < 0 || best == 0.0) {
+                // the row carries nothing: mark it used and take the smallest unused row
+                if (t == 0) urow[i] = 1;
+                __syncthreads();
+                int64_t ni = -1;
+                for (int64_t q = t; q < m; q += ACA_T)
+                    if (!urow[q]) { ni = q; break; }
+                // smallest index: use argmax on -index
+                double key = ni >= 0 ? -(double)ni : -1.0;
+                int64_t kidx = ni;
+                block_argmax(key, kidx, redv, redi);
+                if (kidx < 0) break;
+                i = kidx;
+                continue;
+            }
+            const int64_t jp = bj;
+            if (k >= MAXK) {
+                if (t == 0) atomicOr(A.status, DEV_LIST_OVERFLOW);
+                break;
+            }
+            // --- new cross: v = r / r_{j*}, u(i') = A(i', j*) - sum_l v_l(j*) u_l(i') ----
+            const unsigned long long need = (unsigned long long)n + (unsigned long long)m;
+            if (t == 0) {
+                unsigned long long off = atomicAdd(A.pool_top, need);
+                s_off = (off + need <= A.pool_size) ? (long long)off : -1;
+                if (s_off >= 0) vtab[k] = s_off;
+            }
+            __syncthreads();
+            if (s_off < 0) {
+                if (t == 0) { A.retry[atomicAdd(A.retry_ctr, 1)] = (int32_t)x; s_ctl = 2; }
+                __syncthreads();
+                break;
+            }
+            double *Vk = A.pool + vtab[k];
+            double *Uk = Vk + n;
+            const double inv = __ddiv_rn(1.0, r[jp]);
+            for (int64_t j = t; j < n; j += ACA_T) Vk[j] = __dmul_rn(r[j], inv);
+            // v_l . v_k for l < k, and |v_k|^2 (as l = k), canonical order
+            for (int64_t c0 = 0; c0 <= k; c0 += DOT_CHUNK) {
+                double acc[DOT_CHUNK];
+#pragma unroll
+                for (int c = 0; c < DOT_CHUNK; ++c) acc[c] = 0.0;
+                for (int64_t j = t; j < n; j += ACA_T) {
+                    const double v = Vk[j];
+#pragma unroll
+                    for (int c = 0; c < DOT_CHUNK; ++c)
+                        if (c0 + c <= k) acc[c] = __fma_rn(A.pool[vtab[c0 + c] + j], v, acc[c]);
+                }
+#pragma unroll
+                for (int c = 0; c < DOT_CHUNK; ++c) part[c][t] = acc[c];
+                fold_partials(part, DOT_CHUNK);
+                if (t == 0)
+                    for (int c = 0; c < DOT_CHUNK && c0 + c <= k; ++c) dvv[c0 + c] = part[c][0];
+                __syncthreads();
+            }
+            // u column
+            for (int64_t l = t; l < k; l += ACA_T) sv_l[l] = A.pool[vtab[l] + jp];
+            if (t < d) yj[t] = A.xs[(int64_t)t * N + cols[jp]];
+            __syncthreads();
+            for (int64_t q = t; q < m; q += ACA_T) {
+                double xq[4];
+                load_point(A.xs, N, d, rows[q], xq);
+                double s = kern_exact(A.kp, xq, yj);
+                for (int64_t l = 0; l < k; ++l) s = __fma_rn(-sv_l[l], A.pool[vtab[l] + n + q], s);
+                Uk[q] = s;
+            }
+            __syncthreads();
+            for (int64_t c0 = 0; c0 <= k; c0 += DOT_CHUNK) {
+                double acc[DOT_CHUNK];
+#pragma unroll
+                for (int c = 0; c < DOT_CHUNK; ++c) acc[c] = 0.0;
+                for (int64_t q = t; q < m; q += ACA_T) {
+                    const double u = Uk[q];
+#pragma unroll
+                    for (int c = 0; c < DOT_CHUNK; ++c)
+                        if (c0 + c <= k) acc[c] = __fma_rn(A.pool[vtab[c0 + c] + n + q], u, acc[c]);
+                }
+#pragma unroll
+                for (int c = 0; c < DOT_CHUNK; ++c) part[c][t] = acc[c];
+                fold_partials(part, DOT_CHUNK);
+                if (t == 0)
+                    for (int c = 0; c < DOT_CHUNK && c0 + c <= k; ++c) duu[c0 + c] = part[c][0];
+                __syncthreads();
+            }
+            // Frobenius norm with the new cross, stopping rule (the cross that meets it is not kept)
+            if (t == 0) {
+                double cross = 0.0;
+                for (int64_t l = 0; l < k; ++l) cross = __fma_rn(duu[l], dvv[l], cross);
+                const double nu2 = duu[k], nv2 = dvv[k];
+                double f2 = __dadd_rn(frob2, __dmul_rn(2.0, cross));
+                f2 = __dadd_rn(f2, __dmul_rn(nu2, nv2));
+                const bool stop = __dmul_rn(__dsqrt_rn(nu2), __dsqrt_rn(nv2)) <= __dmul_rn(A.eps, __dsqrt_rn(f2));
+                if (stop) {
+                    s_ctl = 1;
+                } else {
+                    urow[i] = 1;
+                    ucol[jp >> 6] |= 1ull << (jp & 63);
+                    prow[k] = (int32_t)i;
+                    pcol[k] = (int32_t)jp;
+                    redv[0] = f2;   // broadcast the new norm
+                    s_ctl = 0;
+                }
+            }
+            __syncthreads();
+            if (s_ctl == 1) break;
+            frob2 = redv[0];
+            ++k;
+            __syncthreads();
+            if (k == kmax) break;
+            // next row: argmax over unused rows of |u_k|
+            double bv = -1.0;
+            int64_t bi = -1;
+            for (int64_t q = t; q < m; q += ACA_T)
+                if (!urow[q] && fabs(Uk[q]) > bv) { bv = fabs(Uk[q]); bi = q; }
+            block_argmax(bv, bi, redv, redi);
+            if (bi < 0) break;
+            i = bi;
+        }
+        __syncthreads();
+        if (s_ctl != 2 && t == 0) A.rank[x] = (int32_t)k;
+        __syncthreads();
+    }
+}
+
+// ---- bases by LU of the pivot block ---------------------------------------
+struct TransferArgs {
+    KParams kp;
+    int d;
+    int64_t N;
+    const double *xs;
+    const int64_t *row_off;      // candidate rows per cell
+    const int32_t *rows;
+    const int64_t *piv_off;      // compact pivots
+    const int32_t *prow_pt, *pcol_pt;   // point positions
+    const int32_t *prow_loc;     // local row index of each pivot (into the candidate rows)
+    const int32_t *pass;
+    const int64_t *op_off;
+    double *op;
+    const int64_t *lu_off;       // r*r scratch per cell
+    double *lu;
+    int32_t *ipiv;               // r per cell (at piv_off)
+    unsigned *status;
+};
+
+__global__ void __launch_bounds__(256) k_transfer(TransferArgs T, int64_t cnt) {
+    __shared__ double redv[8];
+    __shared__ long long redi[8];
+    const int t = threadIdx.x;
+    for (int64_t x = blockIdx.x; x < cnt; x += gridDim.x) {
+        const int64_t m = T.row_off[x + 1] - T.row_off[x];
+        const int64_t r = T.piv_off[x + 1] - T.piv_off[x];
+        double *op = T.op + T.op_off[x];
+        if (T.pass[x]) {
+            for (int64_t e = t; e < m * m; e += 256) op[e] = (e / m == e % m) ? 1.0 : 0.0;
+            continue;
+        }
+        if (r == 0) continue;
+        const int32_t *tau = T.prow_pt + T.piv_off[x];
+        const int32_t *sig = T.pcol_pt + T.piv_off[x];
+        const int32_t *rows = T.rows + T.row_off[x];
+        double *L = T.lu + T.lu_off[x];
+        int32_t *ip = T.ipiv + T.piv_off[x];
+        // L = M^T, M(a, b) = A(tau_a, sigma_b):  L(a, c) = K(x_{tau_c}, x_{sigma_a})
+        for (int64_t e = t; e < r * r; e += 256) {
+            const int64_t a = e / r, c = e % r;
+            double p[4], q[4];
+            load_point(T.xs, T.N, T.d, tau[c], p);
+            load_point(T.xs, T.N, T.d, sig[a], q);
+            L[e] = kern_exact(T.kp, p, q);
+        }
+        __syncthreads();
+        for (int64_t c = 0; c < r; ++c) {
+            double bv = -1.0;
+            int64_t bi = -1;
+            for (int64_t a = c + t; a < r; a += 256)
+                if (fabs(L[a * r + c]) > bv) { bv = fabs(L[a * r + c]); bi = a; }
+            block_argmax(bv, bi, redv, redi);
+            const int64_t p = bi;
+            if (t == 0) {
+                ip[c] = (int32_t)p;
+                if (L[p * r + c] == 0.0) atomicOr(T.status, DEV_ZERO_PIVOT);
+            }
+            if (p != c)
+                for (int64_t j = t; j < r; j += 256) {
+                    double tmp = L[c * r + j];
+                    L[c * r + j] = L[p * r + j];
+                    L[p * r + j] = tmp;
+                }
+            __syncthreads();
+            const double piv = L[c * r + c];
+            for (int64_t a = c + 1 + t; a < r; a += 256) L[a * r + c] = __ddiv_rn(L[a * r + c], piv);
+            __syncthreads();
+            const int64_t w = r - c - 1;
+            for (int64_t e = t; e < w * w; e += 256) {
+                const int64_t a = c + 1 + e / w, j = c + 1 + e % w;
+                L[a * r + j] = __fma_rn(-L[a * r + c], L[c * r + j], L[a * r + j]);
+            }
+            __syncthreads();
+        }
+        // one candidate row per thread: b = A(t~_row, sigma), swaps, forward, back
+        for (int64_t row = t; row < m; row += 256) {
+            double *b = op + row * r;
+            double p[4], q[4];
+            load_point(T.xs, T.N, T.d, rows[row], p);
+            for (int64_t a = 0; a < r; ++a) {
+                load_point(T.xs, T.N, T.d, sig[a], q);
+                b[a] = kern_exact(T.kp, p, q);
+            }
+            for (int64_t c = 0; c < r; ++c) {
+                const int64_t pc = ip[c];
+                if (pc != c) { double tmp = b[c]; b[c] = b[pc]; b[pc] = tmp; }
+            }
+            for (int64_t a = 0; a < r; ++a) {
+                double s = b[a];
+                for (int64_t j = 0; j < a; ++j) s = __fma_rn(-L[a * r + j], b[j], s);
+                b[a] = s;
+            }
+            for (int64_t a = r - 1; a >= 0; --a) {
+                double s = b[a];
+                for (int64_t j = a + 1; j < r; ++j) s = __fma_rn(-L[a * r + j], b[j], s);
+                b[a] = __ddiv_rn(s, L[a * r + a]);
+            }
+        }
+        __syncthreads();
+        // rows at the pivots are the identity
+        const int32_t *loc = T.prow_loc + T.piv_off[x];
+        for (int64_t e = t; e < r * r; e += 256) {
+            const int64_t a = e / r, c = e % r;
+            op[(int64_t)loc[a] * r + c] = (a == c) ? 1.0 : 0.0;
+        }
+        __syncthreads();
+    }
+}
+
+// compact per-cell ACA outputs (capacity layout) into the level's pivot CSR
+__global__ void k_compact_pivots(int64_t cnt, const int64_t *cap_off, const int32_t *rank, const int64_t *poff,
+                                 const int64_t *row_off, const int64_t *col_off, const int32_t *rows,
+                                 const int32_t *cols, const int32_t *prow_loc_cap, const int32_t *pcol_loc_cap,
+                                 int32_t *prow_pt, int32_t *pcol_pt, int32_t *prow_loc) {
+    for (int64_t x = blockIdx.x; x < cnt; x += gridDim.x) {
+        const int64_t r = rank[x];
+        for (int64_t a = threadIdx.x; a < r; a += blockDim.x) {
+            const int32_t li = prow_loc_cap[cap_off[x] + a];
+            const int32_t lj = pcol_loc_cap[cap_off[x] + a];
+            prow_loc[poff[x] + a] = li;
+            prow_pt[poff[x] + a] = rows[row_off[x] + li];
+            pcol_pt[poff[x] + a] = lj >= 0 ? cols[col_off[x] + lj] : -1;
+        }
+    }
+}
+
+__global__ void k_ranks_i64(int64_t cnt, const int32_t *rank, int64_t *out) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < cnt; x += (int64_t)gridDim.x * blockDim.x)
+        out[x] = rank[x];
+}
+
+__global__ void k_sizes_prod(int64_t cnt, const int64_t *a_off, const int32_t *rank, const int32_t *pass, int64_t *out,
+                             int square) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < cnt; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = a_off[x + 1] - a_off[x];
+        const int64_t r = rank[x];
+        out[x] = square ? (pass[x] ? 0 : r * r) : m * r;
+    }
+}
+
+__global__ void k_cap_sizes(int64_t cnt, const int64_t *msz, const int64_t *nsz, int64_t *cap, int32_t *pass) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < cnt; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = msz[x], n = nsz[x];
+        cap[x] = n == 0 ? m : (m < n ? m : n);
+        pass[x] = n == 0 ? 1 : 0;
+    }
+}
+
+__global__ void k_iota(int32_t *a, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = (int32_t)i;
+}
+
+}  // namespace
+
+// Per-level outputs kept until build_finish assembles the global arrays.
+struct LevelOut {
+    int64_t cnt = 0;
+    int64_t *row_off = nullptr;     // candidate rows (cnt + 1)
+    int32_t *rows = nullptr;
+    int64_t *piv_off = nullptr;     // (cnt + 1)
+    int32_t *prow_pt = nullptr, *pcol_pt = nullptr;
+    int32_t *pass = nullptr, *rank = nullptr;
+    int64_t *op_off = nullptr;      // (cnt + 1)
+    double *op = nullptr;
+    int64_t npiv = 0, nrows = 0, nop = 0;
+};
+
+void build_pivots_impl(Handle *h, std::vector<LevelOut> &lv, Scratch &keep) {
+    cudaStream_t s = h->stream;
+    const int kappa = h->kappa;
+    lv.assign(kappa + 1, LevelOut{});
+    size_t free_b = 0, total_b = 0;
+    NNCA_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    int dev = 0, nsm = 152;
+    NNCA_CUDA(cudaGetDevice(&dev));
+    NNCA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    int aca_per_sm = 1;
+    NNCA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&aca_per_sm, k_aca, ACA_T, 0));
+    aca_per_sm = std::max(1, aca_per_sm);
+
+    for (int l = kappa; l >= h->lmin; --l) {
+        Scratch scr;
+        const int64_t b0 = h->level_base[l], b1 = h->level_base[l + 1], cnt = b1 - b0;
+        const int leaf = (l == kappa);
+        LevelOut &L = lv[l];
+        L.cnt = cnt;
+        const LevelOut *C = leaf ? nullptr : &lv[l + 1];
+        const int64_t cb0 = leaf ? 0 : h->level_base[l + 1];
+        int64_t *msz = scr.get<int64_t>(cnt + 1), *nsz = scr.get<int64_t>(cnt + 1);
+        k_cand_sizes<<<grid_for(cnt, 128), 128, 0, s>>>(b0, b1, leaf, h->cbeg, h->cend, h->cch_beg, h->cch_end,
+                                                        h->il_off, h->il_idx, leaf ? nullptr : C->rank, cb0, msz, nsz);
+        NNCA_LAUNCH_CHECK();
+        int64_t *cap = scr.get<int64_t>(cnt + 1);
+        L.pass = (int32_t *)keep.get<int32_t>(cnt);
+        L.rank = (int32_t *)keep.get<int32_t>(cnt);
+        k_cap_sizes<<<grid_for(cnt, 256), 256, 0, s>>>(cnt, msz, nsz, cap, L.pass);
+        NNCA_LAUNCH_CHECK();
+        L.row_off = keep.get<int64_t>(cnt + 1);
+        NNCA_CUDA(cudaMemcpyAsync(L.row_off, msz, cnt * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+        NNCA_CUDA(cudaMemsetAsync(L.row_off + cnt, 0, sizeof(int64_t), s));
+        L.nrows = scan_total_i64(L.row_off, L.row_off, cnt + 1, s, scr);
+        int64_t *col_off = scr.get<int64_t>(cnt + 1);
+        NNCA_CUDA(cudaMemcpyAsync(col_off, nsz, cnt * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+        NNCA_CUDA(cudaMemsetAsync(col_off + cnt, 0, sizeof(int64_t), s));
+        const int64_t ncols = scan_total_i64(col_off, col_off, cnt + 1, s, scr);
+        NNCA_CUDA(cudaMemsetAsync(cap + cnt, 0, sizeof(int64_t), s));
+        const int64_t ncap = scan_total_i64(cap, cap, cnt + 1, s, scr);
+        NNCA_REQUIRE(L.nrows < (1ll << 31) && ncols < (1ll << 40), NNCA_ERR_UNSUPPORTED, "candidate sets too large");
+        L.rows = keep.get<int32_t>(L.nrows);
+        int32_t *cols = scr.get<int32_t>(ncols);
+        k_cand_gather<<<grid_for(cnt * 32, 256), 256, 0, s>>>(b0, b1, leaf, h->cbeg, h->cend, h->cch_beg, h->cch_end,
+                                                              h->il_off, h->il_idx, leaf ? nullptr : C->piv_off,
+                                                              leaf ? nullptr : C->prow_pt, cb0, L.row_off, col_off,
+                                                              L.rows, cols);
+        NNCA_LAUNCH_CHECK();
+
+        // ACA with a scratch pool; cells that find the pool exhausted are re-run
+        int32_t *prow_cap = scr.get<int32_t>(ncap), *pcol_cap = scr.get<int32_t>(ncap);
+        int32_t *work = scr.get<int32_t>(cnt), *retry = scr.get<int32_t>(cnt);
+        int *ctrs = scr.get<int>(2);
+        unsigned long long *ptop = scr.get<unsigned long long>(1);
+        k_iota<<<grid_for(cnt, 256), 256, 0, s>>>(work, cnt);
+        NNCA_LAUNCH_CHECK();
+        NNCA_CUDA(cudaStreamSynchronize(s));
+        NNCA_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        // pool: the worst case of every cell if that fits, else most of free memory
+        std::vector<int64_t> hm(cnt), hn(cnt);
+        NNCA_CUDA(cudaMemcpy(hm.data(), msz, cnt * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        NNCA_CUDA(cudaMemcpy(hn.data(), nsz, cnt * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        unsigned long long worst = 0, biggest = 0;
+        for (int64_t x = 0; x < cnt; ++x) {
+            if (hn[x] == 0 || hm[x] == 0) continue;
+            unsigned long long kx = (unsigned long long)std::min(hm[x], hn[x]);
+            unsigned long long need = hn[x] + (hn[x] + 63) / 64 + (hm[x] + 7) / 8 + (kx + 1) * (hn[x] + hm[x]);
+            worst += need;
+            biggest = std::max(biggest, need);
+        }
+        unsigned long long avail = (unsigned long long)(free_b * 0.7) / sizeof(double);
+        unsigned long long pool_words = std::max<unsigned long long>(std::min(worst, avail), 1);
+        NNCA_REQUIRE(biggest <= pool_words || worst == 0, NNCA_ERR_OOM, "one cell's ACA scratch exceeds device memory");
+        double *pool = scr.get<double>(pool_words);
+        int nwork = (int)cnt;
+        int rounds = 0;
+        while (nwork > 0) {
+            NNCA_CUDA(cudaMemsetAsync(ctrs, 0, 2 * sizeof(int), s));
+            NNCA_CUDA(cudaMemsetAsync(ptop, 0, sizeof(unsigned long long), s));
+            AcaArgs A{};
+            A.kp = h->kp;
+            A.d = h->d;
+            A.N = h->n;
+            A.xs = h->xs;
+            A.eps = h->cfg.aca_tol;
+            A.row_off = L.row_off;
+            A.col_off = col_off;
+            A.cap_off = cap;
+            A.rows = L.rows;
+            A.cols = cols;
+            A.rank = L.rank;
+            A.prow = prow_cap;
+            A.pcol = pcol_cap;
+            A.work = work;
+            A.nwork = nwork;
+            A.work_ctr = ctrs;
+            A.retry = retry;
+            A.retry_ctr = ctrs + 1;
+            A.pool = pool;
+            A.pool_size = pool_words;
+            A.pool_top = ptop;
+            A.status = h->dev_status;
+            const unsigned grid = (unsigned)std::min<int64_t>(nwork, (int64_t)nsm * aca_per_sm);
+            k_aca<<<grid, ACA_T, 0, s>>>(A);
+            NNCA_LAUNCH_CHECK();
+            int nretry = 0;
+            NNCA_CUDA(cudaMemcpyAsync(&nretry, ctrs + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+            NNCA_CUDA(cudaStreamSynchronize(s));
+            NNCA_REQUIRE(nretry < nwork, NNCA_ERR_OOM, "ACA scratch pool too small for one cell");
+            if (nretry > 0) {
+                h->stats.aca_retries += nretry;
+                NNCA_CUDA(cudaMemcpyAsync(work, retry, nretry * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+            }
+            nwork = nretry;
+            ++rounds;
+        }
+        const unsigned st = read_status(h);
+        NNCA_REQUIRE(!(st & DEV_LIST_OVERFLOW), NNCA_ERR_UNSUPPORTED, "a cell's rank exceeds the supported maximum");
+
+        // compact pivots
+        L.piv_off = keep.get<int64_t>(cnt + 1);
+        k_ranks_i64<<<grid_for(cnt, 256), 256, 0, s>>>(cnt, L.rank, L.piv_off);
+        NNCA_LAUNCH_CHECK();
+        NNCA_CUDA(cudaMemsetAsync(L.piv_off + cnt, 0, sizeof(int64_t), s));
+        L.npiv = scan_total_i64(L.piv_off, L.piv_off, cnt + 1, s, scr);
+        L.prow_pt = keep.get<int32_t>(L.npiv);
+        L.pcol_pt = keep.get<int32_t>(L.npiv);
+        int32_t *prow_loc = scr.get<int32_t>(L.npiv);
+        k_compact_pivots<<<grid_for(cnt * 64, 64), 64, 0, s>>>(cnt, cap, L.rank, L.piv_off, L.row_off, col_off, L.rows,
+                                                               cols, prow_cap, pcol_cap, L.prow_pt, L.pcol_pt, prow_loc);
+        NNCA_LAUNCH_CHECK();
+
+        // bases
+        L.op_off = keep.get<int64_t>(cnt + 1);
+        k_sizes_prod<<<grid_for(cnt, 256), 256, 0, s>>>(cnt, L.row_off, L.rank, L.pass, L.op_off, 0);
+        NNCA_LAUNCH_CHECK();
+        NNCA_CUDA(cudaMemsetAsync(L.op_off + cnt, 0, sizeof(int64_t), s));
+        L.nop = scan_total_i64(L.op_off, L.op_off, cnt + 1, s, scr);
+        L.op = keep.get<double>(L.nop);
+        int64_t *lu_off = scr.get<int64_t>(cnt + 1);
+        k_sizes_prod<<<grid_for(cnt, 256), 256, 0, s>>>(cnt, L.row_off, L.rank, L.pass, lu_off, 1);
+        NNCA_LAUNCH_CHECK();
+        NNCA_CUDA(cudaMemsetAsync(lu_off + cnt, 0, sizeof(int64_t), s));
+        const int64_t nlu = scan_total_i64(lu_off, lu_off, cnt + 1, s, scr);
+        scr.release(pool);
+        TransferArgs T{};
+        T.kp = h->kp;
+        T.d = h->d;
+        T.N = h->n;
+        T.xs = h->xs;
+        T.row_off = L.row_off;
+        T.rows = L.rows;
+        T.piv_off = L.piv_off;
+        T.prow_pt = L.prow_pt;
+        T.pcol_pt = L.pcol_pt;
+        T.prow_loc = prow_loc;
+        T.pass = L.pass;
+        T.op_off = L.op_off;
+        T.op = L.op;
+        T.lu_off = lu_off;
+        T.lu = scr.get<double>(nlu);
+        T.ipiv = scr.get<int32_t>(L.npiv);
+        T.status = h->dev_status;
+        k_transfer<<<(unsigned)std::min<int64_t>(cnt, (int64_t)nsm * 8), 256, 0, s>>>(T, cnt);
+        NNCA_LAUNCH_CHECK();
+        NNCA_CUDA(cudaStreamSynchronize(s));
+    }
+}
+
+
+namespace {
+
+__global__ void k_level_scatter_i32(int64_t cnt, int64_t b0, const int32_t *src, int32_t *dst) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < cnt; x += (int64_t)gridDim.x * blockDim.x)
+        dst[b0 + x] = src[x];
+}
+
+__global__ void k_level_scatter_off(int64_t cnt, int64_t b0, int64_t base, const int64_t *src, int64_t *dst) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x <= cnt; x += (int64_t)gridDim.x * blockDim.x)
+        dst[b0 + x] = base + src[x];
+}
+
+__global__ void k_fill_off(int64_t from, int64_t to, int64_t v, int64_t *dst) {
+    for (int64_t x = from + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < to; x += (int64_t)gridDim.x * blockDim.x)
+        dst[x] = v;
+}
+
+__global__ void k_off_to_i32(int64_t n, const int64_t *src, int32_t *dst) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
+        dst[x] = (int32_t)src[x];
+}
+
+// cell centres: corner + (coord + 0.5) * side / 2^l
+__global__ void k_centres(int64_t b0, int64_t b1, int l, int d, int64_t ncell, const int32_t *ccoord, double c0,
+                          double c1, double c2, double c3, double side, double *ccen) {
+    const double corner[4] = {c0, c1, c2, c3};
+    const double w = ldexp(side, -l);
+    for (int64_t c = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < b1; c += (int64_t)gridDim.x * blockDim.x)
+        for (int k = 0; k < d; ++k) ccen[(int64_t)k * ncell + c] = corner[k] + ((double)ccoord[(int64_t)k * ncell + c] + 0.5) * w;
+}
+
+// pivot coordinates (FP64) and relative to their cell's centre (FP32)
+__global__ void k_pivot_coords(int64_t b0, int64_t b1, int d, int64_t N, int64_t ncell, int64_t npiv,
+                               const int32_t *piv_off, const int32_t *piv_row, const double *xs, const double *ccen,
+                               double *pv64, float *pv32) {
+    for (int64_t c = b0 + blockIdx.x; c < b1; c += gridDim.x)
+        for (int64_t p = piv_off[c] + threadIdx.x; p < piv_off[c + 1]; p += blockDim.x)
+            for (int k = 0; k < d; ++k) {
+                const double v = xs[(int64_t)k * N + piv_row[p]];
+                pv64[(int64_t)k * npiv + p] = v;
+                pv32[(int64_t)k * npiv + p] = (float)(v - ccen[(int64_t)k * ncell + c]);
+            }
+}
+
+// leaf of every point, and coordinates relative to the leaf centre (FP32)
+__global__ void k_leaf_coords(int64_t b0, int64_t b1, int d, int64_t N, int64_t ncell, const int32_t *cbeg,
+                              const int32_t *cend, const double *xs, const double *ccen, int32_t *leaf_of, float *xs32) {
+    for (int64_t c = b0 + blockIdx.x; c < b1; c += gridDim.x)
+        for (int64_t i = cbeg[c] + threadIdx.x; i < cend[c]; i += blockDim.x) {
+            leaf_of[i] = (int32_t)c;
+            for (int k = 0; k < d; ++k)
+                xs32[(int64_t)k * N + i] = (float)(xs[(int64_t)k * N + i] - ccen[(int64_t)k * ncell + c]);
+        }
+}
+
+// work counts: m2l pairs per target cell, p2p pairs per leaf
+__global__ void k_work_counts(int64_t b0, int64_t b1, int64_t leaf0, const int32_t *il_off, const int32_t *il_idx,
+                              const int32_t *nb_off, const int32_t *nb_idx, const int32_t *piv_off,
+                              const int32_t *cbeg, const int32_t *cend, int64_t *m2l_w, int64_t *p2p_w,
+                              unsigned long long *tot) {
+    for (int64_t c = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < b1; c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = piv_off[c + 1] - piv_off[c], s = 0;
+        for (int32_t q = il_off[c]; q < il_off[c + 1]; ++q) s += piv_off[il_idx[q] + 1] - piv_off[il_idx[q]];
+        m2l_w[c] = r * s;
+        atomicAdd(&tot[0], (unsigned long long)(r * s));
+        if (c >= leaf0) {
+            int64_t nb = cend[c] - cbeg[c], t = 0;
+            for (int32_t q = nb_off[c]; q < nb_off[c + 1]; ++q) t += cend[nb_idx[q]] - cbeg[nb_idx[q]];
+            p2p_w[c - leaf0] = nb * t;
+            atomicAdd(&tot[1], (unsigned long long)(nb * t));
+        }
+    }
+}
+
+}  // namespace
+
+void build_pivots(Handle *h) {
+    cudaStream_t s = h->stream;
+    Scratch keep;
+    std::vector<LevelOut> lv;
+    build_pivots_impl(h, lv, keep);
+    const int kappa = h->kappa;
+    const int64_t nc = h->ncell;
+    Scratch scr;
+
+    // global CSR of pivots, candidates and operators (levels above lmin hold nothing)
+    int64_t *poff = scr.get<int64_t>(nc + 1);
+    h->cand_off = dalloc<int64_t>(h, nc + 1);
+    h->op_off = dalloc<int64_t>(h, nc + 1);
+    h->passthru = dalloc<int32_t>(h, nc);
+    NNCA_CUDA(cudaMemsetAsync(h->passthru, 0, nc * sizeof(int32_t), s));
+    int64_t npiv = 0, nrows = 0, nop = 0;
+    for (int l = 0; l <= kappa; ++l) {
+        const int64_t b0 = h->level_base[l], cnt = h->level_base[l + 1] - b0;
+        if (l < h->lmin) {
+            k_fill_off<<<grid_for(cnt + 1, 256), 256, 0, s>>>(b0, b0 + cnt + 1, npiv, poff);
+            k_fill_off<<<grid_for(cnt + 1, 256), 256, 0, s>>>(b0, b0 + cnt + 1, nrows, h->cand_off);
+            k_fill_off<<<grid_for(cnt + 1, 256), 256, 0, s>>>(b0, b0 + cnt + 1, nop, h->op_off);
+            NNCA_LAUNCH_CHECK();
+            continue;
+        }
+        const LevelOut &L = lv[l];
+        k_level_scatter_off<<<grid_for(cnt + 1, 256), 256, 0, s>>>(cnt, b0, npiv, L.piv_off, poff);
+        k_level_scatter_off<<<grid_for(cnt + 1, 256), 256, 0, s>>>(cnt, b0, nrows, L.row_off, h->cand_off);
+        k_level_scatter_off<<<grid_for(cnt + 1, 256), 256, 0, s>>>(cnt, b0, nop, L.op_off, h->op_off);
+        k_level_scatter_i32<<<grid_for(cnt, 256), 256, 0, s>>>(cnt, b0, L.pass, h->passthru);
+        NNCA_LAUNCH_CHECK();
+        npiv += L.npiv;
+        nrows += L.nrows;
+        nop += L.nop;
+    }
+    NNCA_REQUIRE(npiv < (1ll << 31), NNCA_ERR_UNSUPPORTED, "more than 2^31 pivots");
+    h->npiv = npiv;
+    h->nop = nop;
+    h->piv_off = dalloc<int32_t>(h, nc + 1);
+    k_off_to_i32<<<grid_for(nc + 1, 256), 256, 0, s>>>(nc + 1, poff, h->piv_off);
+    NNCA_LAUNCH_CHECK();
+    h->piv_row = dalloc<int32_t>(h, npiv);
+    h->piv_col = dalloc<int32_t>(h, npiv);
+    h->op = dalloc<double>(h, nop);
+    int64_t ep = 0, eo = 0;
+    for (int l = h->lmin; l <= kappa; ++l) {
+        const LevelOut &L = lv[l];
+        if (L.npiv) {
+            NNCA_CUDA(cudaMemcpyAsync(h->piv_row + ep, L.prow_pt, L.npiv * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+            NNCA_CUDA(cudaMemcpyAsync(h->piv_col + ep, L.pcol_pt, L.npiv * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        }
+        if (L.nop) NNCA_CUDA(cudaMemcpyAsync(h->op + eo, L.op, L.nop * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        ep += L.npiv;
+        eo += L.nop;
+    }
+    h->h_piv_off.resize(nc + 1);
+    NNCA_CUDA(cudaMemcpyAsync(h->h_piv_off.data(), h->piv_off, (nc + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    NNCA_CUDA(cudaStreamSynchronize(s));
+}
+
+void build_finish(Handle *h) {
+    cudaStream_t s = h->stream;
+    Scratch scr;
+    const int d = h->d, kappa = h->kappa;
+    const int64_t nc = h->ncell, N = h->n;
+    h->ccen = dalloc<double>(h, (size_t)nc * d);
+    double cr[4] = {0, 0, 0, 0};
+    for (int k = 0; k < d; ++k) cr[k] = h->corner[k];
+    for (int l = 0; l <= kappa; ++l) {
+        const int64_t b0 = h->level_base[l], b1 = h->level_base[l + 1];
+        k_centres<<<grid_for(b1 - b0, 256), 256, 0, s>>>(b0, b1, l, d, nc, h->ccoord, cr[0], cr[1], cr[2], cr[3], h->side,
+                                                         h->ccen);
+        NNCA_LAUNCH_CHECK();
+    }
+    h->pv64 = dalloc<double>(h, (size_t)h->npiv * d);
+    h->pv32 = dalloc<float>(h, (size_t)h->npiv * d);
+    if (h->npiv) {
+        k_pivot_coords<<<(unsigned)std::min<int64_t>(nc, 152 * 64), 64, 0, s>>>(0, nc, d, N, nc, h->npiv, h->piv_off,
+                                                                               h->piv_row, h->xs, h->ccen, h->pv64,
+                                                                               h->pv32);
+        NNCA_LAUNCH_CHECK();
+    }
+    const int64_t leaf0 = h->level_base[kappa], leaf1 = h->level_base[kappa + 1];
+    h->nleaf = leaf1 - leaf0;
+    h->leaf_of = dalloc<int32_t>(h, N);
+    h->xs32 = dalloc<float>(h, (size_t)N * d);
+    k_leaf_coords<<<(unsigned)std::min<int64_t>(h->nleaf, 152 * 64), 64, 0, s>>>(leaf0, leaf1, d, N, nc, h->cbeg,
+                                                                                 h->cend, h->xs, h->ccen, h->leaf_of,
+                                                                                 h->xs32);
+    NNCA_LAUNCH_CHECK();
+
+    // work lists, heaviest first: M2L target cells and leaves for the near field
+    int64_t *m2l_w = scr.get<int64_t>(nc), *p2p_w = scr.get<int64_t>(h->nleaf);
+    unsigned long long *tot = scr.get<unsigned long long>(2);
+    NNCA_CUDA(cudaMemsetAsync(tot, 0, 2 * sizeof(unsigned long long), s));
+    k_work_counts<<<grid_for(nc, 128), 128, 0, s>>>(0, nc, leaf0, h->il_off, h->il_idx, h->nb_off, h->nb_idx,
+                                                    h->piv_off, h->cbeg, h->cend, m2l_w, p2p_w, tot);
+    NNCA_LAUNCH_CHECK();
+    std::vector<int64_t> hw(nc), hp(h->nleaf);
+    unsigned long long ht[2];
+    NNCA_CUDA(cudaMemcpyAsync(hw.data(), m2l_w, nc * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    NNCA_CUDA(cudaMemcpyAsync(hp.data(), p2p_w, h->nleaf * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    NNCA_CUDA(cudaMemcpyAsync(ht, tot, sizeof(ht), cudaMemcpyDeviceToHost, s));
+    NNCA_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> tg;
+    for (int64_t c = 0; c < nc; ++c)
+        if (hw[c] > 0) tg.push_back((int32_t)c);
+    std::stable_sort(tg.begin(), tg.end(), [&](int32_t a, int32_t b) { return hw[a] > hw[b]; });
+    h->n_m2l_tgt = (int64_t)tg.size();
+    h->m2l_tgt = dalloc<int32_t>(h, tg.size());
+    if (!tg.empty())
+        NNCA_CUDA(cudaMemcpyAsync(h->m2l_tgt, tg.data(), tg.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    std::vector<int32_t> lo(h->nleaf);
+    for (int64_t c = 0; c < h->nleaf; ++c) lo[c] = (int32_t)(leaf0 + c);
+    std::stable_sort(lo.begin(), lo.end(), [&](int32_t a, int32_t b) { return hp[a - leaf0] > hp[b - leaf0]; });
+    h->leaf_order = dalloc<int32_t>(h, lo.size());
+    NNCA_CUDA(cudaMemcpyAsync(h->leaf_order, lo.data(), lo.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    h->stats.m2l_pairs = (int64_t)ht[0];
+    h->stats.p2p_pairs = (int64_t)ht[1];
+    NNCA_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace nnca

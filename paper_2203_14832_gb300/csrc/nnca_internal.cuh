@@ -1,0 +1,265 @@
+// Internal definitions of the NNCA CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/nnca.h"
+
+namespace nnca {
+
+// ---------------------------------------------------------------------------
+// Errors: internal code throws nnca::Error; the C ABI converts it to a status.
+struct Error : std::runtime_error {
+    nnca_status status;
+    Error(nnca_status s, const std::string &m) : std::runtime_error(m), status(s) {}
+};
+
+#define NNCA_CUDA(call)                                                                     \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            cudaGetLastError();                                                             \
+            throw ::nnca::Error(e_ == cudaErrorMemoryAllocation ? NNCA_ERR_OOM : NNCA_ERR_CUDA, \
+                                std::string(#call) + ": " + cudaGetErrorString(e_));       \
+        }                                                                                   \
+    } while (0)
+
+#define NNCA_LAUNCH_CHECK() NNCA_CUDA(cudaGetLastError())
+
+#define NNCA_REQUIRE(cond, st, msg)                     \
+    do {                                                \
+        if (!(cond)) throw ::nnca::Error((st), (msg));  \
+    } while (0)
+
+// Device-side status word bits (never a trap: a kernel that finds a problem
+// records it and returns; the host reads the word and reports it).
+enum : unsigned {
+    DEV_OK = 0,
+    DEV_POOL_EXHAUSTED = 1u,   // a cell ran out of ACA scratch: it is retried
+    DEV_BAD_INDEX = 2u,        // an index failed a bounds check
+    DEV_ZERO_PIVOT = 4u,       // the LU of a pivot block met an exact zero pivot
+    DEV_LIST_OVERFLOW = 8u
+};
+
+inline unsigned ceil_div(unsigned long long a, unsigned long long b) { return (unsigned)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// Kernel functions K(x, y). Parameters passed by value to every kernel.
+struct KParams {
+    int kind;
+    int d;
+    double s;      // scale
+    double h;      // h or a
+    double diag;   // A(i, i)
+    float sf, hf;
+};
+
+// FP64 form that performs exactly the IEEE operations of the oracle's kernel
+// definition (each operation rounded on its own, correctly rounded sqrt and
+// division), so that pivot decisions are reproducible bit for bit. The log and
+// exp kernels use CUDA's log/exp, which may differ from the host library in
+// the last place.
+__device__ __forceinline__ double kern_exact(const KParams &kp, const double *x, const double *y) {
+    double r2 = 0.0;
+    if (kp.kind != NNCA_K_SEPARABLE && kp.kind != NNCA_K_POLY2) {
+        for (int k = 0; k < kp.d; ++k) {
+            double t = __dsub_rn(x[k], y[k]);
+            r2 = __dadd_rn(r2, __dmul_rn(t, t));
+        }
+    }
+    switch (kp.kind) {
+    case NNCA_K_LOG:
+        if (r2 == 0.0) return 0.0;
+        return __dmul_rn(kp.s, log(__dsqrt_rn(r2)));
+    case NNCA_K_INV_R:
+        if (r2 == 0.0) return 0.0;
+        return __ddiv_rn(kp.s, __dsqrt_rn(r2));
+    case NNCA_K_GAUSS:
+        return __dmul_rn(kp.s, exp(__ddiv_rn(-r2, __dmul_rn(__dmul_rn(2.0, kp.h), kp.h))));
+    case NNCA_K_MATERN:
+        return __dmul_rn(kp.s, exp(__ddiv_rn(-__dsqrt_rn(r2), kp.h)));
+    case NNCA_K_PAPER_I: {
+        double r = __dsqrt_rn(r2);
+        if (r == 0.0) return 0.0;
+        if (r < kp.h)
+            return __dmul_rn(kp.s, __ddiv_rn(__dmul_rn(r, __dsub_rn(log(r), 1.0)),
+                                             __dmul_rn(kp.h, __dsub_rn(log(kp.h), 1.0))));
+        return __dmul_rn(kp.s, __ddiv_rn(log(r), log(kp.h)));
+    }
+    case NNCA_K_PAPER_II: {
+        double r = __dsqrt_rn(r2);
+        if (r < kp.h) return __dmul_rn(kp.s, __ddiv_rn(r, kp.h));
+        return __dmul_rn(kp.s, __ddiv_rn(kp.h, r));
+    }
+    case NNCA_K_SEPARABLE: {
+        double fx = 1.0, fy = 1.0;
+        for (int k = 0; k < kp.d; ++k) {
+            fx = __dadd_rn(fx, x[k]);
+            fy = __dadd_rn(fy, y[k]);
+        }
+        return __dmul_rn(kp.s, __dmul_rn(fx, fy));
+    }
+    case NNCA_K_POLY2: {
+        double t = 1.0;
+        for (int k = 0; k < kp.d; ++k) t = __dadd_rn(t, __dmul_rn(x[k], y[k]));
+        return __dmul_rn(kp.s, __dmul_rn(t, t));
+    }
+    default:
+        return 0.0;
+    }
+}
+
+// K as a function of r^2 (radial kernels) or of the points (the two
+// non-radial test kernels), FP64, for the product. Contraction allowed.
+__device__ __forceinline__ double kern64_r2(const KParams &kp, double r2) {
+    switch (kp.kind) {
+    case NNCA_K_INV_R: return r2 > 0.0 ? kp.s * rsqrt(r2) : 0.0;
+    case NNCA_K_LOG: return r2 > 0.0 ? 0.5 * kp.s * log(r2) : 0.0;
+    case NNCA_K_GAUSS: return kp.s * exp(-r2 / (2.0 * kp.h * kp.h));
+    case NNCA_K_MATERN: return kp.s * exp(-sqrt(r2) / kp.h);
+    case NNCA_K_PAPER_I: {
+        if (!(r2 > 0.0)) return 0.0;
+        double r = sqrt(r2);
+        if (r < kp.h) return kp.s * (r * (log(r) - 1.0)) / (kp.h * (log(kp.h) - 1.0));
+        return kp.s * log(r) / log(kp.h);
+    }
+    case NNCA_K_PAPER_II: {
+        double r = sqrt(r2);
+        return r < kp.h ? kp.s * r / kp.h : kp.s * kp.h / r;
+    }
+    default: return 0.0;
+    }
+}
+
+__device__ __forceinline__ float kern32_r2(const KParams &kp, float r2) {
+    switch (kp.kind) {
+    case NNCA_K_INV_R: return r2 > 0.f ? kp.sf * rsqrtf(r2) : 0.f;
+    case NNCA_K_LOG: return r2 > 0.f ? 0.5f * kp.sf * __logf(r2) : 0.f;
+    case NNCA_K_GAUSS: return kp.sf * __expf(-r2 / (2.f * kp.hf * kp.hf));
+    case NNCA_K_MATERN: return kp.sf * __expf(-sqrtf(r2) / kp.hf);
+    case NNCA_K_PAPER_I: {
+        if (!(r2 > 0.f)) return 0.f;
+        float r = sqrtf(r2);
+        if (r < kp.hf) return kp.sf * (r * (logf(r) - 1.f)) / (kp.hf * (logf(kp.hf) - 1.f));
+        return kp.sf * logf(r) / logf(kp.hf);
+    }
+    case NNCA_K_PAPER_II: {
+        float r = sqrtf(r2);
+        return r < kp.hf ? kp.sf * r / kp.hf : kp.sf * kp.hf / r;
+    }
+    default: return 0.f;
+    }
+}
+
+inline bool kernel_is_radial(int kind) { return kind != NNCA_K_SEPARABLE && kind != NNCA_K_POLY2; }
+
+// ---------------------------------------------------------------------------
+// Handle.
+struct Handle;
+
+// Device allocation tracked by the handle (freed by nnca_destroy).
+void *dev_alloc(Handle *h, size_t bytes);
+void dev_free(Handle *h, void *p);
+template <class T> T *dalloc(Handle *h, size_t count) { return (T *)dev_alloc(h, sizeof(T) * (count ? count : 1)); }
+
+// Scratch allocation owned by the caller of a build step (freed explicitly).
+struct Scratch {
+    std::vector<void *> ptrs;
+    ~Scratch() { for (void *p : ptrs) cudaFree(p); }
+    template <class T> T *get(size_t count) {
+        void *p = nullptr;
+        cudaError_t e = cudaMalloc(&p, sizeof(T) * (count ? count : 1));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw Error(NNCA_ERR_OOM, std::string("scratch cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        ptrs.push_back(p);
+        return (T *)p;
+    }
+    void release(void *p) {
+        for (auto &q : ptrs) if (q == p) { cudaFree(q); q = nullptr; }
+    }
+};
+
+struct Handle {
+    nnca_config cfg{};
+    KParams kp{};
+    int d = 0, lmax = 0, kappa = 0, lmin = 0;
+    int64_t n = 0;
+    double corner[4] = {0, 0, 0, 0};
+    double side = 1.0;
+    cudaStream_t stream = nullptr;
+
+    // tree (device)
+    int32_t *perm = nullptr;      // [n] original index of sorted position
+    uint64_t *keys = nullptr;     // [n]
+    double *xs = nullptr;         // [d][n] sorted coordinates (SoA)
+    int64_t ncell = 0;
+    std::vector<int64_t> level_base;   // host, kappa + 2 entries
+    uint64_t *ckey = nullptr;
+    int32_t *cbeg = nullptr, *cend = nullptr, *cpar = nullptr, *cch_beg = nullptr, *cch_end = nullptr;
+    int32_t *ccoord = nullptr;    // [d][ncell] integer cell coordinates at the cell's level
+
+    // lists (device CSR over global cell ids)
+    int32_t *nb_off = nullptr, *nb_idx = nullptr, *il_off = nullptr, *il_idx = nullptr;
+    int64_t n_nb = 0, n_il = 0;
+
+    // pivots and operators (device)
+    int32_t *piv_off = nullptr, *piv_row = nullptr, *piv_col = nullptr, *passthru = nullptr;
+    int64_t *cand_off = nullptr, *op_off = nullptr;
+    double *op = nullptr;
+    int64_t npiv = 0, nop = 0;
+    std::vector<int32_t> h_piv_off;    // host copy (ncell + 1)
+
+    // product data (device)
+    double *ccen = nullptr;       // [d][ncell] cell centres
+    double *pv64 = nullptr;       // [d][npiv] pivot coordinates
+    float *pv32 = nullptr;        // [d][npiv] pivot coordinates relative to their cell centre
+    float *xs32 = nullptr;        // [d][n] point coordinates relative to their leaf centre
+    int32_t *leaf_of = nullptr;   // [n] leaf (global id) of each sorted position
+    int32_t *m2l_tgt = nullptr;   // cells with a non-empty IL, heaviest first
+    int64_t n_m2l_tgt = 0;
+    int32_t *leaf_order = nullptr;  // leaves, heaviest near field first
+    int64_t nleaf = 0;
+
+    // product workspace
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    int64_t ws_nrhs = 0;
+    void *host_stage = nullptr;   // device buffers for nnca_matvec_host
+    size_t host_stage_bytes = 0;
+
+    // per-pass profiling of the product
+    bool profile = false;
+    std::vector<cudaEvent_t> prof_events;   // 6 per profiled product, pending
+    std::vector<cudaEvent_t> event_pool;
+    int64_t launches = 0;
+
+    std::vector<void *> allocs;
+    std::string last_error;
+    nnca_stats stats{};
+    unsigned *dev_status = nullptr;   // device status word
+};
+
+// Build steps (tree.cu, lists.cu, aca.cu) and product (matvec.cu).
+void build_tree(Handle *h, const double *P, int layout);
+void build_lists(Handle *h);
+void build_pivots(Handle *h);   // pivots, bases, global pivot/operator arrays
+void build_finish(Handle *h);   // data of the product: centres, FP32 coordinates, work lists
+void matvec(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int dtype, int precision);
+
+// Exclusive scan of n uint32/int64 values (scan.cu). out may alias in.
+void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s, Scratch &scr);
+int64_t scan_total_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s, Scratch &scr);
+
+unsigned read_status(Handle *h);
+// Record the profiling event that ends pass `slot` (0 = start of the product).
+void prof_mark(Handle *h, int slot);
+
+}  // namespace nnca
