@@ -756,13 +756,19 @@ __global__ void k_off_to_i32(int64_t n, const int64_t *src, int32_t *dst) {
         dst[x] = (int32_t)src[x];
 }
 
-// cell centres: corner + (coord + 0.5) * side / 2^l
+// cell centres: corner + (coord + 0.5) * side / 2^l, in FP64 and as a float hi/lo pair
 __global__ void k_centres(int64_t b0, int64_t b1, int l, int d, int64_t ncell, const int32_t *ccoord, double c0,
-                          double c1, double c2, double c3, double side, double *ccen) {
+                          double c1, double c2, double c3, double side, double *ccen, float *chi, float *clo) {
     const double corner[4] = {c0, c1, c2, c3};
     const double w = ldexp(side, -l);
     for (int64_t c = b0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < b1; c += (int64_t)gridDim.x * blockDim.x)
-        for (int k = 0; k < d; ++k) ccen[(int64_t)k * ncell + c] = corner[k] + ((double)ccoord[(int64_t)k * ncell + c] + 0.5) * w;
+        for (int k = 0; k < d; ++k) {
+            const double v = corner[k] + ((double)ccoord[(int64_t)k * ncell + c] + 0.5) * w;
+            const float hi = (float)v;
+            ccen[(int64_t)k * ncell + c] = v;
+            chi[(int64_t)k * ncell + c] = hi;
+            clo[(int64_t)k * ncell + c] = (float)(v - (double)hi);
+        }
 }
 
 // pivot coordinates (FP64) and relative to their cell's centre (FP32)
@@ -787,6 +793,43 @@ __global__ void k_leaf_coords(int64_t b0, int64_t b1, int d, int64_t N, int64_t 
             for (int k = 0; k < d; ++k)
                 xs32[(int64_t)k * N + i] = (float)(xs[(int64_t)k * N + i] - ccen[(int64_t)k * ncell + c]);
         }
+}
+
+// packed data of the FP32 product
+__global__ void k_pack_cells(int64_t nc, int d, const int32_t *piv_off, const double *ccen, int2 *prange, float4 *chi,
+                             float4 *clo) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc; c += (int64_t)gridDim.x * blockDim.x) {
+        prange[c] = make_int2(piv_off[c], piv_off[c + 1] - piv_off[c]);
+        float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+        for (int k = 0; k < d && k < 3; ++k) {
+            const double v = ccen[(int64_t)k * nc + c];
+            h[k] = (float)v;
+            l[k] = (float)(v - (double)h[k]);
+        }
+        chi[c] = make_float4(h[0], h[1], h[2], 0.f);
+        clo[c] = make_float4(l[0], l[1], l[2], 0.f);
+    }
+}
+
+__global__ void k_pack_points(int64_t n, int64_t npiv, int d, const double *xs, const float *pv32, float4 *xh,
+                              float4 *xl, float4 *pv4) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n || i < npiv; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < n) {
+            float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+            for (int k = 0; k < d && k < 3; ++k) {
+                const double v = xs[(int64_t)k * n + i];
+                h[k] = (float)v;
+                l[k] = (float)(v - (double)h[k]);
+            }
+            xh[i] = make_float4(h[0], h[1], h[2], 0.f);
+            xl[i] = make_float4(l[0], l[1], l[2], 0.f);
+        }
+        if (i < npiv) {
+            float p[3] = {0.f, 0.f, 0.f};
+            for (int k = 0; k < d && k < 3; ++k) p[k] = pv32[(int64_t)k * npiv + i];
+            pv4[i] = make_float4(p[0], p[1], p[2], 0.f);
+        }
+    }
 }
 
 // work counts: m2l pairs per target cell, p2p pairs per leaf
@@ -876,12 +919,14 @@ void build_finish(Handle *h) {
     const int d = h->d, kappa = h->kappa;
     const int64_t nc = h->ncell, N = h->n;
     h->ccen = dalloc<double>(h, (size_t)nc * d);
+    h->ccen_hi = dalloc<float>(h, (size_t)nc * d);
+    h->ccen_lo = dalloc<float>(h, (size_t)nc * d);
     double cr[4] = {0, 0, 0, 0};
     for (int k = 0; k < d; ++k) cr[k] = h->corner[k];
     for (int l = 0; l <= kappa; ++l) {
         const int64_t b0 = h->level_base[l], b1 = h->level_base[l + 1];
         k_centres<<<grid_for(b1 - b0, 256), 256, 0, s>>>(b0, b1, l, d, nc, h->ccoord, cr[0], cr[1], cr[2], cr[3], h->side,
-                                                         h->ccen);
+                                                         h->ccen, h->ccen_hi, h->ccen_lo);
         NNCA_LAUNCH_CHECK();
     }
     h->pv64 = dalloc<double>(h, (size_t)h->npiv * d);
@@ -929,6 +974,74 @@ void build_finish(Handle *h) {
     NNCA_CUDA(cudaMemcpyAsync(h->leaf_order, lo.data(), lo.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     h->stats.m2l_pairs = (int64_t)ht[0];
     h->stats.p2p_pairs = (int64_t)ht[1];
+
+    // FP32 product: packed arrays and work items. A cell's targets form items of
+    // 32; the remainder c < 32 gets S = 2^s lanes per target (c * S <= 32, S <= 16),
+    // which split its sources. Items are ordered heaviest first.
+    h->prange = dalloc<int2>(h, nc);
+    h->chi4 = dalloc<float4>(h, nc);
+    h->clo4 = dalloc<float4>(h, nc);
+    h->xh4 = dalloc<float4>(h, N);
+    h->xl4 = dalloc<float4>(h, N);
+    h->pv4 = dalloc<float4>(h, h->npiv);
+    k_pack_cells<<<grid_for(nc, 256), 256, 0, s>>>(nc, d, h->piv_off, h->ccen, h->prange, h->chi4, h->clo4);
+    NNCA_LAUNCH_CHECK();
+    k_pack_points<<<grid_for(std::max<int64_t>(N, h->npiv), 256), 256, 0, s>>>(N, h->npiv, d, h->xs, h->pv32, h->xh4,
+                                                                                h->xl4, h->pv4);
+    NNCA_LAUNCH_CHECK();
+    std::vector<int32_t> hpo(h->h_piv_off);
+    std::vector<int32_t> hcb(nc), hce(nc);
+    NNCA_CUDA(cudaMemcpy(hcb.data(), h->cbeg, nc * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    NNCA_CUDA(cudaMemcpy(hce.data(), h->cend, nc * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    auto make_items = [&](const std::vector<int32_t> &cells, const std::vector<int64_t> &count,
+                          const std::vector<int64_t> &weight, int2 **dst, int *ndst) {
+        std::vector<std::pair<int64_t, int2>> lists[5];
+        for (size_t k = 0; k < cells.size(); ++k) {
+            const int64_t cnt = count[k];
+            NNCA_REQUIRE(cnt < 65536, NNCA_ERR_UNSUPPORTED, "a cell with 65536 or more targets");
+            int64_t a0 = 0;
+            for (; a0 + 32 <= cnt; a0 += 32) lists[0].push_back({weight[k], make_int2(cells[k], (int)(a0 | (32 << 16)))});
+            const int64_t rem = cnt - a0;
+            if (rem > 0) {
+                int ls = 0;
+                while (ls < 4 && rem * (2 << ls) <= 32) ++ls;
+                lists[ls].push_back({weight[k] >> ls, make_int2(cells[k], (int)(a0 | (rem << 16)))});
+            }
+        }
+        for (int ls = 0; ls < 5; ++ls) {
+            std::stable_sort(lists[ls].begin(), lists[ls].end(),
+                             [](const std::pair<int64_t, int2> &x, const std::pair<int64_t, int2> &y) { return x.first > y.first; });
+            std::vector<int2> v;
+            for (auto &p : lists[ls]) v.push_back(p.second);
+            ndst[ls] = (int)v.size();
+            dst[ls] = dalloc<int2>(h, v.size());
+            if (!v.empty())
+                NNCA_CUDA(cudaMemcpy(dst[ls], v.data(), v.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        }
+    };
+    {
+        std::vector<int32_t> cells;
+        std::vector<int64_t> count, weight;
+        for (int64_t c = 0; c < nc; ++c)
+            if (hw[c] > 0) {
+                const int64_t r = hpo[c + 1] - hpo[c];
+                cells.push_back((int32_t)c);
+                count.push_back(r);
+                weight.push_back(hw[c] / std::max<int64_t>(r, 1));
+            }
+        make_items(cells, count, weight, h->m2l_items, h->n_m2l_items);
+    }
+    {
+        std::vector<int32_t> cells;
+        std::vector<int64_t> count, weight;
+        for (int64_t c = leaf0; c < leaf1; ++c) {
+            const int64_t nb = hce[c] - hcb[c];
+            cells.push_back((int32_t)c);
+            count.push_back(nb);
+            weight.push_back(hp[c - leaf0] / std::max<int64_t>(nb, 1));
+        }
+        make_items(cells, count, weight, h->leaf_items, h->n_leaf_items);
+    }
     NNCA_CUDA(cudaStreamSynchronize(s));
 }
 

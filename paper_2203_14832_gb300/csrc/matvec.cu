@@ -31,22 +31,43 @@ namespace nnca {
 
 namespace {
 
+// Single-instruction MUFU forms (flush-to-zero approximations).
+__device__ __forceinline__ float mufu_rsqrt(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float mufu_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float mufu_lg2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // f(r^2) with K = s f(r); FP32 and FP64 forms, one instantiation per kernel.
+// f32_far: r^2 > 0 guaranteed (distinct cells); f32: any r^2 >= 0.
 template <int KIND> struct KF;
 template <> struct KF<NNCA_K_INV_R> {
-    static __device__ __forceinline__ float f32(const KParams &, float r2) { return r2 > 0.f ? rsqrtf(r2) : 0.f; }
-    static __device__ __forceinline__ float f32_far(const KParams &, float r2) { return rsqrtf(r2); }
+    static __device__ __forceinline__ float f32(const KParams &, float r2) { return r2 > 0.f ? mufu_rsqrt(r2) : 0.f; }
+    static __device__ __forceinline__ float f32_far(const KParams &, float r2) { return mufu_rsqrt(r2); }
     static __device__ __forceinline__ double f64(const KParams &, double r2) { return r2 > 0.0 ? rsqrt(r2) : 0.0; }
 };
 template <> struct KF<NNCA_K_LOG> {
-    static __device__ __forceinline__ float f32(const KParams &, float r2) { return r2 > 0.f ? 0.5f * __logf(r2) : 0.f; }
-    static __device__ __forceinline__ float f32_far(const KParams &, float r2) { return 0.5f * __logf(r2); }
+    // 0.5 ln(r^2) = (0.5 ln 2) log2(r^2)
+    static __device__ __forceinline__ float f32(const KParams &, float r2) {
+        return r2 > 0.f ? 0.34657359f * mufu_lg2(r2) : 0.f;
+    }
+    static __device__ __forceinline__ float f32_far(const KParams &, float r2) { return 0.34657359f * mufu_lg2(r2); }
     static __device__ __forceinline__ double f64(const KParams &, double r2) { return r2 > 0.0 ? 0.5 * log(r2) : 0.0; }
 };
 template <> struct KF<NNCA_K_GAUSS> {
     // exp(-r^2 / (2 h^2)) = 2^(r^2 * c), c = -log2(e) / (2 h^2) precomputed in kp.hf
-    static __device__ __forceinline__ float f32(const KParams &kp, float r2) { return exp2f(r2 * kp.hf); }
-    static __device__ __forceinline__ float f32_far(const KParams &kp, float r2) { return exp2f(r2 * kp.hf); }
+    static __device__ __forceinline__ float f32(const KParams &kp, float r2) { return mufu_ex2(r2 * kp.hf); }
+    static __device__ __forceinline__ float f32_far(const KParams &kp, float r2) { return mufu_ex2(r2 * kp.hf); }
     static __device__ __forceinline__ double f64(const KParams &kp, double r2) { return exp(-r2 / (2.0 * kp.h * kp.h)); }
 };
 template <> struct KF<NNCA_K_MATERN> {
@@ -109,7 +130,7 @@ __global__ void k_perm_in(const TI *x, int64_t ld, int64_t N, int64_t nrhs, cons
 template <class T, int NR>
 __global__ void k_upward(int64_t b0, int64_t b1, int leaf, const int32_t *cbeg, const int32_t *cend,
                          const int32_t *cch_beg, const int32_t *cch_end, const int32_t *piv_off, const int64_t *op_off,
-                         const T *op, const T *xt, int64_t N, T *w, int64_t npiv) {
+                         const T *op, const T *xt, int64_t N, T *w, int64_t npiv, float *w32) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -138,7 +159,15 @@ __global__ void k_upward(int64_t b0, int64_t b1, int leaf, const int32_t *cbeg, 
                 for (int q = 0; q < NR; ++q) acc[q] += c * src[q * ld + a];
             }
 #pragma unroll
-            for (int q = 0; q < NR; ++q) w[q * npiv + piv_off[B] + b] = acc[q];
+            for (int q = 0; q < NR; ++q) {
+                w[q * npiv + piv_off[B] + b] = acc[q];
+                if (w32) {
+                    // w = hi + lo in float: the M2L sums keep w to ~1e-14 relative
+                    const float hi = (float)acc[q];
+                    w32[q * npiv + piv_off[B] + b] = hi;
+                    w32[(q + NR) * npiv + piv_off[B] + b] = (float)((double)acc[q] - (double)hi);
+                }
+            }
         }
     }
 }
@@ -228,71 +257,374 @@ __global__ void __launch_bounds__(32 * MV_WARPS) k_m2l_f64(KParams kp, int d, co
     }
 }
 
+// ---- packed FP32 arithmetic (two lanes of float in one 64-bit register) ------
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 f2_unpack(f2 a) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a));
+    return r;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// f(r^2) on a packed pair; SAFE maps r^2 = 0 to f(0) of the singular kernels (0).
+#ifndef NNCA_RSQRT_NEWTON
+#define NNCA_RSQRT_NEWTON 0
+#endif
+template <int KIND, bool SAFE> struct KF2 {
+    static __device__ __forceinline__ f2 eval(const KParams &kp, f2 r2) {
+        const float2 v = f2_unpack(r2);
+        return f2_pack(SAFE ? KF<KIND>::f32(kp, v.x) : KF<KIND>::f32_far(kp, v.x),
+                       SAFE ? KF<KIND>::f32(kp, v.y) : KF<KIND>::f32_far(kp, v.y));
+    }
+};
+template <bool SAFE> struct KF2<NNCA_K_INV_R, SAFE> {
+    // 1/r: one MUFU rsqrt (relative error ~1e-7). An optional Newton step
+    // f <- f - (f/2)(r^2 f^2 - 1) takes it to float rounding, at 4 more packed
+    // operations per pair; measured, it changes the product's error by ~3%.
+    static __device__ __forceinline__ f2 eval(const KParams &, f2 r2) {
+        const float2 v = f2_unpack(r2);
+        f2 f = f2_pack(mufu_rsqrt(v.x), mufu_rsqrt(v.y));
+#if NNCA_RSQRT_NEWTON
+        const f2 h = f2_mul(r2, f);
+        const f2 e = f2_fma(h, f, f2_pack(-1.f, -1.f));
+        const f2 hf = f2_mul(f, f2_pack(-0.5f, -0.5f));
+        f = f2_fma(hf, e, f);
+#endif
+        if (SAFE) {
+            float2 g = f2_unpack(f);
+            g.x = v.x > 0.f ? g.x : 0.f;
+            g.y = v.y > 0.f ? g.y : 0.f;
+            f = f2_pack(g.x, g.y);
+        }
+        return f;
+    }
+};
+
+// ---- FP32 source streaming -----------------------------------------------------
+// A warp streams the sources of its source cells through a 64-entry ring in
+// shared memory and evaluates them in full chunks of 32. Sources are stored in
+// pairs, [x0 x1 y0 y1][z0 z1 w0 w1] (and, for the near field, the low parts
+// [xl0 xl1 yl0 yl1][zl0 zl1 - -]), so one 128-bit load yields two packed
+// operands. Only the last chunk of a work item is padded, with far-away
+// sources of weight 0. A work item is up to 32/S targets of one cell; each
+// target is served by S lanes that split every chunk's sources between them.
+constexpr int RING = 64;
+constexpr float FAR_AWAY = 1.0e18f;
+
+// LO: near field, low parts of the coordinates in slots 2-3. !LO: far field,
+// low part of the weight in slot 2 ([wl0 wl1 - -]).
+template <bool LO> struct Ring2 {
+    float4 v[RING / 2][LO ? 4 : 3];
+};
+
+template <int KIND, int LOGS, bool SAFE, bool LO>
+struct Stream2 {
+    static constexpr int S = 1 << LOGS;
+    Ring2<LO> &R;
+    int fill = 0, done = 0;
+    const int s;             // this lane's slice
+    f2 tx, ty, tz, txl, tyl, tzl;
+    float sum = 0.f, comp = 0.f;
+    __device__ Stream2(Ring2<LO> &r, int slice, float x, float y, float z, float xl, float yl, float zl)
+        : R(r), s(slice) {
+        tx = f2_pack(x, x);
+        ty = f2_pack(y, y);
+        tz = f2_pack(z, z);
+        txl = f2_pack(xl, xl);
+        tyl = f2_pack(yl, yl);
+        tzl = f2_pack(zl, zl);
+    }
+    __device__ __forceinline__ void eval_chunk(const KParams &kp) {
+        const int base = (done & (RING - 1)) >> 1;   // source-pair index of the chunk
+        f2 acc = 0ull, acc2 = 0ull;
+#pragma unroll
+        for (int i = 0; i < 16 / S; ++i) {
+            const int q = base + s + S * i;
+            const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(&R.v[q][0]);
+            const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(&R.v[q][1]);
+            f2 dx = f2_sub(A.x, tx), dy = f2_sub(A.y, ty), dz = f2_sub(B.x, tz);
+            f2 wlo = 0ull;
+            if (!LO) wlo = *reinterpret_cast<const f2 *>(&R.v[q][2]);
+            if (LO) {
+                const ulonglong2 C = *reinterpret_cast<const ulonglong2 *>(&R.v[q][2]);
+                const ulonglong2 D = *reinterpret_cast<const ulonglong2 *>(&R.v[q][3]);
+                dx = f2_add(dx, f2_sub(C.x, txl));
+                dy = f2_add(dy, f2_sub(C.y, tyl));
+                dz = f2_add(dz, f2_sub(D.x, tzl));
+            }
+            f2 r2 = f2_mul(dx, dx);
+            r2 = f2_fma(dy, dy, r2);
+            r2 = f2_fma(dz, dz, r2);
+            const f2 fv = KF2<KIND, SAFE>::eval(kp, r2);
+            if (i & 1) acc2 = f2_fma(fv, B.y, acc2);
+            else acc = f2_fma(fv, B.y, acc);
+            if (!LO) acc2 = f2_fma(fv, wlo, acc2);
+        }
+        const float2 a = f2_unpack(f2_add(acc, acc2));
+        two_sum_add(sum, comp, a.x + a.y);
+    }
+    __device__ __forceinline__ void flush_full(const KParams &kp) {
+        if (fill - done >= 32) {
+            __syncwarp();
+            eval_chunk(kp);
+            done += 32;
+        }
+    }
+    // lanes < n push one source each
+    __device__ __forceinline__ void push(const KParams &kp, int lane, int n, float x, float y, float z, float w,
+                                         float xl, float yl, float zl) {
+        __syncwarp();
+        if (lane < n) {
+            const int pos = (fill + lane) & (RING - 1);
+            float *p = reinterpret_cast<float *>(&R.v[pos >> 1][0]);
+            const int h = pos & 1;
+            p[0 + h] = x;
+            p[2 + h] = y;
+            p[4 + h] = z;
+            p[6 + h] = w;
+            if (LO) {
+                p[8 + h] = xl;
+                p[10 + h] = yl;
+                p[12 + h] = zl;
+            } else {
+                p[8 + h] = xl;   // far field: the low part of the weight
+            }
+        }
+        fill += n;
+        flush_full(kp);
+    }
+    __device__ __forceinline__ void finish(const KParams &kp, int lane) {
+        if (fill > done) push(kp, lane, done + 32 - fill, FAR_AWAY, FAR_AWAY, FAR_AWAY, 0.f, 0.f, 0.f, 0.f);
+    }
+    // combine the S slices of every target (lanes t*S .. t*S + S-1) into the first
+    __device__ __forceinline__ double result() {
+#pragma unroll
+        for (int o = 1; o < S; o <<= 1) {
+            const float so = __shfl_xor_sync(0xffffffffu, sum, o);
+            const float co = __shfl_xor_sync(0xffffffffu, comp, o);
+            two_sum_add(sum, comp, so);
+            comp += co;
+        }
+        return (double)sum + (double)comp;
+    }
+};
+
+// Work item: cell, first target, number of targets, log2 of the slices.
+__device__ __forceinline__ void unpack_item(int2 it, int &cell, int &a0, int &c) {
+    cell = it.x;
+    a0 = it.y & 0xffff;
+    c = (it.y >> 16) & 0xff;
+}
+
 // ---- M2L, FP32 evaluation -----------------------------------------------------
-template <int KIND, int NR>
-__global__ void __launch_bounds__(32 * MV_WARPS) k_m2l_f32(KParams kp, int d, const int32_t *tgt, int64_t ntgt,
+template <int KIND, int LOGS>
+__global__ void __launch_bounds__(32 * MV_WARPS) k_m2l_f32(KParams kp, const int2 *items, int nitems,
                                                           const int32_t *il_off, const int32_t *il_idx,
-                                                          const int32_t *piv_off, const float *pv, int64_t npiv,
-                                                          const double *ccen, int64_t ncell, const double *w,
-                                                          double *u) {
-    __shared__ float4 sx[MV_WARPS][32];
-    __shared__ float sw[MV_WARPS][NR][32];
+                                                          const int2 *prange, const float4 *pv4,
+                                                          const float4 *chi, const float4 *clo, const float *w,
+                                                          const float *wlo, double *u) {
+    __shared__ __align__(16) Ring2<false> ring[MV_WARPS];
+    constexpr int S = 1 << LOGS;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int64_t warp = blockIdx.x * (int64_t)MV_WARPS + wl;
-    const int64_t nw = (int64_t)gridDim.x * MV_WARPS;
-    for (int64_t t = warp; t < ntgt; t += nw) {
-        const int64_t X = tgt[t];
-        const int64_t p0 = piv_off[X], rX = piv_off[X + 1] - p0;
-        double cX[3] = {0, 0, 0};
-        for (int k = 0; k < d && k < 3; ++k) cX[k] = ccen[(int64_t)k * ncell + X];
-        for (int64_t a0 = 0; a0 < rX; a0 += 32) {
-            const int64_t a = a0 + lane;
-            const bool act = a < rX;
-            float xa[3] = {0.f, 0.f, 0.f};
-            if (act)
-                for (int k = 0; k < d && k < 3; ++k) xa[k] = pv[(int64_t)k * npiv + p0 + a];
-            float s[NR], c[NR];
-#pragma unroll
-            for (int q = 0; q < NR; ++q) { s[q] = 0.f; c[q] = 0.f; }
-            for (int32_t e = il_off[X]; e < il_off[X + 1]; ++e) {
-                const int64_t Y = il_idx[e];
-                const int64_t q0 = piv_off[Y], rY = piv_off[Y + 1] - q0;
-                float sh[3] = {0.f, 0.f, 0.f};
-                for (int k = 0; k < d && k < 3; ++k) sh[k] = (float)(ccen[(int64_t)k * ncell + Y] - cX[k]);
-                for (int64_t b0 = 0; b0 < rY; b0 += 32) {
-                    const int64_t nb = min((int64_t)32, rY - b0);
-                    __syncwarp();
-                    if (lane < nb) {
-                        const int64_t p = q0 + b0 + lane;
-                        float4 v;
-                        v.x = d > 0 ? pv[p] + sh[0] : 0.f;
-                        v.y = d > 1 ? pv[npiv + p] + sh[1] : 0.f;
-                        v.z = d > 2 ? pv[2 * npiv + p] + sh[2] : 0.f;
-                        v.w = 0.f;
-                        sx[wl][lane] = v;
-#pragma unroll
-                        for (int q = 0; q < NR; ++q) sw[wl][q][lane] = (float)w[q * npiv + p];
-                    }
-                    __syncwarp();
-                    float part[NR];
-#pragma unroll
-                    for (int q = 0; q < NR; ++q) part[q] = 0.f;
-#pragma unroll 4
-                    for (int j = 0; j < nb; ++j) {
-                        const float4 v = sx[wl][j];
-                        const float dx = v.x - xa[0], dy = v.y - xa[1], dz = v.z - xa[2];
-                        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                        const float f = KF<KIND>::f32_far(kp, r2);
-#pragma unroll
-                        for (int q = 0; q < NR; ++q) part[q] = fmaf(f, sw[wl][q][j], part[q]);
-                    }
-#pragma unroll
-                    for (int q = 0; q < NR; ++q) two_sum_add(s[q], c[q], part[q]);
+    const int t = lane >> LOGS, s = lane & (S - 1);
+    for (int it = blockIdx.x * MV_WARPS + wl; it < nitems; it += gridDim.x * MV_WARPS) {
+        int X, a0, c;
+        unpack_item(items[it], X, a0, c);
+        const int2 pr = prange[X];
+        const bool act = t < c;
+        const float4 xa = act ? pv4[pr.x + a0 + t] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 hX = chi[X], lX = clo[X];
+        Stream2<KIND, LOGS, false, false> st(ring[wl], s, xa.x, xa.y, xa.z, 0.f, 0.f, 0.f);
+        const int e1 = il_off[X + 1];
+        for (int e0 = il_off[X]; e0 < e1; e0 += 32) {
+            // headers of up to 32 interaction-list cells, one per lane
+            const int ne = min(32, e1 - e0);
+            int2 pk = make_int2(0, 0);
+            float shx = 0.f, shy = 0.f, shz = 0.f;
+            if (lane < ne) {
+                const int Y = il_idx[e0 + lane];
+                pk = prange[Y];
+                const float4 hY = chi[Y], lY = clo[Y];
+                shx = (hY.x - hX.x) + (lY.x - lX.x);
+                shy = (hY.y - hX.y) + (lY.y - lX.y);
+                shz = (hY.z - hX.z) + (lY.z - lX.z);
+            }
+            // walk the chunks of 32 sources, loading the next chunk before pushing the current
+            int k = 0, b0 = 0;
+            int p0 = __shfl_sync(0xffffffffu, pk.x, 0), rY = __shfl_sync(0xffffffffu, pk.y, 0);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            float wv = 0.f, wl = 0.f;
+            int n = min(32, rY);
+            if (lane < n) {
+                v = pv4[p0 + lane];
+                wv = w[p0 + lane];
+                wl = wlo[p0 + lane];
+            }
+            while (k < ne) {
+                const float sx = __shfl_sync(0xffffffffu, shx, k), sy = __shfl_sync(0xffffffffu, shy, k),
+                            sz = __shfl_sync(0xffffffffu, shz, k);
+                // next chunk
+                int k2 = k, b2 = b0 + 32;
+                if (b2 >= rY) { k2 = k + 1; b2 = 0; }
+                int p2 = p0, r2n = rY;
+                if (k2 != k && k2 < ne) {
+                    p2 = __shfl_sync(0xffffffffu, pk.x, k2);
+                    r2n = __shfl_sync(0xffffffffu, pk.y, k2);
+                } else if (k2 != k) {
+                    r2n = 0;
+                }
+                const int n2 = k2 < ne ? min(32, r2n - b2) : 0;
+                float4 v2 = make_float4(0.f, 0.f, 0.f, 0.f);
+                float w2 = 0.f, wl2 = 0.f;
+                if (lane < n2) {
+                    v2 = pv4[p2 + b2 + lane];
+                    w2 = w[p2 + b2 + lane];
+                    wl2 = wlo[p2 + b2 + lane];
+                }
+                if (n > 0) st.push(kp, lane, n, v.x + sx, v.y + sy, v.z + sz, wv, wl, 0.f, 0.f);
+                k = k2;
+                b0 = b2;
+                p0 = p2;
+                rY = r2n;
+                n = n2;
+                v = v2;
+                wv = w2;
+                wl = wl2;
+            }
+        }
+        st.finish(kp, lane);
+        const double r = st.result();
+        if (act && s == 0) u[pr.x + a0 + t] = kp.s * r;
+    }
+}
+
+// ---- leaves: L2P (FP64) + P2P (FP32 evaluation on hi/lo coordinates) ------------
+// Points carry absolute coordinates as float pairs x = hi + lo. The difference
+// (hi_j - hi_i) + (lo_j - lo_i) is exact in its first term whenever the points
+// are close (Sterbenz), so close pairs keep full relative accuracy.
+template <int KIND, int LOGS, class TO>
+__global__ void __launch_bounds__(32 * MV_WARPS) k_leaf_f32(KParams kp, const int2 *items, int nitems,
+                                                           const int32_t *cbeg, const int32_t *cend,
+                                                           const int32_t *nb_off, const int32_t *nb_idx,
+                                                           const int32_t *piv_off, const int64_t *op_off,
+                                                           const double *op, const double *u, const float4 *xh4,
+                                                           const float4 *xl4, const float *xt32, const double *xt64,
+                                                           const int32_t *perm, TO *y) {
+    __shared__ __align__(16) Ring2<true> ring[MV_WARPS];
+    constexpr int S = 1 << LOGS;
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int t = lane >> LOGS, s = lane & (S - 1);
+    const float k0 = KF<KIND>::f32(kp, 0.f);
+    for (int it = blockIdx.x * MV_WARPS + wl; it < nitems; it += gridDim.x * MV_WARPS) {
+        int B, a0, c;
+        unpack_item(items[it], B, a0, c);
+        const int i0 = cbeg[B], nB = cend[B] - i0;
+        const bool act = t < c;
+        const int i = i0 + a0 + t;
+        const float4 th = act ? xh4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 tl = act ? xl4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        // neighbours other than B: distinct cells, r > 0 for every pair
+        Stream2<KIND, LOGS, false, true> st(ring[wl], s, th.x, th.y, th.z, tl.x, tl.y, tl.z);
+        const int e1 = nb_off[B + 1];
+        for (int e0 = nb_off[B]; e0 < e1; e0 += 32) {
+            const int ne = min(32, e1 - e0);
+            int jb = 0, jn = 0;   // point range of the neighbour (empty for B itself)
+            if (lane < ne) {
+                const int Y = nb_idx[e0 + lane];
+                if (Y != B) {
+                    jb = cbeg[Y];
+                    jn = cend[Y] - jb;
                 }
             }
-            if (act)
-#pragma unroll
-                for (int q = 0; q < NR; ++q) u[q * npiv + p0 + a] = kp.s * ((double)s[q] + (double)c[q]);
+            int k = 0, b0 = 0;
+            int j0 = __shfl_sync(0xffffffffu, jb, 0), nY = __shfl_sync(0xffffffffu, jn, 0);
+            int n = min(32, nY);
+            float4 vh = make_float4(0.f, 0.f, 0.f, 0.f), vl = vh;
+            float wv = 0.f;
+            if (lane < n) {
+                vh = xh4[j0 + lane];
+                vl = xl4[j0 + lane];
+                wv = xt32[j0 + lane];
+            }
+            while (k < ne) {
+                int k2 = k, b2 = b0 + 32;
+                int j2 = j0, n2tot = nY;
+                if (b2 >= nY) {
+                    k2 = k + 1;
+                    b2 = 0;
+                    j2 = k2 < ne ? __shfl_sync(0xffffffffu, jb, k2) : 0;
+                    n2tot = k2 < ne ? __shfl_sync(0xffffffffu, jn, k2) : 0;
+                }
+                const int n2 = k2 < ne ? max(0, min(32, n2tot - b2)) : 0;
+                float4 vh2 = make_float4(0.f, 0.f, 0.f, 0.f), vl2 = vh2;
+                float w2 = 0.f;
+                if (lane < n2) {
+                    vh2 = xh4[j2 + b2 + lane];
+                    vl2 = xl4[j2 + b2 + lane];
+                    w2 = xt32[j2 + b2 + lane];
+                }
+                if (n > 0) st.push(kp, lane, n, vh.x, vh.y, vh.z, wv, vl.x, vl.y, vl.z);
+                k = k2;
+                b0 = b2;
+                j0 = j2;
+                nY = n2tot;
+                n = n2;
+                vh = vh2;
+                vl = vl2;
+                wv = w2;
+            }
+        }
+        st.finish(kp, lane);
+        double near = st.result();
+        // the leaf itself: pairs with r = 0 (the diagonal, coincident points) are guarded
+        Stream2<KIND, LOGS, true, true> self(ring[wl], s, th.x, th.y, th.z, tl.x, tl.y, tl.z);
+        for (int b0 = 0; b0 < nB; b0 += 32) {
+            const int n = min(32, nB - b0);
+            float4 vh = make_float4(0.f, 0.f, 0.f, 0.f), vl = vh;
+            float wv = 0.f;
+            if (lane < n) {
+                vh = xh4[i0 + b0 + lane];
+                vl = xl4[i0 + b0 + lane];
+                wv = xt32[i0 + b0 + lane];
+            }
+            self.push(kp, lane, n, vh.x, vh.y, vh.z, wv, vl.x, vl.y, vl.z);
+        }
+        self.finish(kp, lane);
+        near += self.result();
+        if (act && s == 0) {
+            // L2P in FP64
+            const int r = piv_off[B + 1] - piv_off[B];
+            const double *U = op + op_off[B] + (int64_t)(a0 + t) * r;
+            const double *uB = u + piv_off[B];
+            double far = 0.0;
+            for (int b = 0; b < r; ++b) far = fma(U[b], uB[b], far);
+            // the pair (i, i) was evaluated as K(0); the diagonal takes the configured value
+            const double yv = far + kp.s * near + (kp.diag - kp.s * (double)k0) * xt64[i];
+            y[perm[i]] = (TO)yv;
         }
     }
 }
@@ -369,95 +701,6 @@ __global__ void __launch_bounds__(32 * MV_WARPS) k_leaf_f64(KParams kp, int d, c
     }
 }
 
-// ---- leaves: L2P (FP64) + P2P (FP32 evaluation) ---------------------------------
-template <int KIND, int NR, class TO>
-__global__ void __launch_bounds__(32 * MV_WARPS) k_leaf_f32(KParams kp, int d, const int32_t *leaves, int64_t nleaf,
-                                                           const int32_t *cbeg, const int32_t *cend,
-                                                           const int32_t *nb_off, const int32_t *nb_idx,
-                                                           const int32_t *piv_off, const int64_t *op_off,
-                                                           const double *op, const double *u, int64_t npiv,
-                                                           const float *xs32, int64_t N, const double *ccen,
-                                                           int64_t ncell, const float *xt32, const int32_t *perm, TO *y,
-                                                           int64_t ld) {
-    __shared__ float4 sx[MV_WARPS][32];
-    __shared__ float sw[MV_WARPS][NR][32];
-    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int64_t warp = blockIdx.x * (int64_t)MV_WARPS + wl;
-    const int64_t nw = (int64_t)gridDim.x * MV_WARPS;
-    const float k0 = KF<KIND>::f32(kp, 0.f);
-    for (int64_t t = warp; t < nleaf; t += nw) {
-        const int64_t B = leaves[t];
-        const int64_t i0 = cbeg[B], nB = cend[B] - i0;
-        const int64_t r = piv_off[B + 1] - piv_off[B];
-        const double *U = op + op_off[B];
-        double cB[3] = {0, 0, 0};
-        for (int k = 0; k < d && k < 3; ++k) cB[k] = ccen[(int64_t)k * ncell + B];
-        for (int64_t a0 = 0; a0 < nB; a0 += 32) {
-            const int64_t a = a0 + lane;
-            const bool act = a < nB;
-            float xa[3] = {0.f, 0.f, 0.f};
-            if (act)
-                for (int k = 0; k < d && k < 3; ++k) xa[k] = xs32[(int64_t)k * N + i0 + a];
-            double far[NR];
-            float s[NR], c[NR];
-#pragma unroll
-            for (int q = 0; q < NR; ++q) { far[q] = 0.0; s[q] = 0.f; c[q] = 0.f; }
-            if (act)
-                for (int64_t b = 0; b < r; ++b) {
-                    const double cc = U[a * r + b];
-#pragma unroll
-                    for (int q = 0; q < NR; ++q) far[q] = fma(cc, u[q * npiv + piv_off[B] + b], far[q]);
-                }
-            for (int32_t e = nb_off[B]; e < nb_off[B + 1]; ++e) {
-                const int64_t Y = nb_idx[e];
-                const int64_t j0 = cbeg[Y], nY = cend[Y] - j0;
-                float sh[3] = {0.f, 0.f, 0.f};
-                for (int k = 0; k < d && k < 3; ++k) sh[k] = (float)(ccen[(int64_t)k * ncell + Y] - cB[k]);
-                for (int64_t b0 = 0; b0 < nY; b0 += 32) {
-                    const int64_t nb = min((int64_t)32, nY - b0);
-                    __syncwarp();
-                    if (lane < nb) {
-                        const int64_t p = j0 + b0 + lane;
-                        float4 v;
-                        v.x = d > 0 ? xs32[p] + sh[0] : 0.f;
-                        v.y = d > 1 ? xs32[N + p] + sh[1] : 0.f;
-                        v.z = d > 2 ? xs32[2 * N + p] + sh[2] : 0.f;
-                        v.w = 0.f;
-                        sx[wl][lane] = v;
-#pragma unroll
-                        for (int q = 0; q < NR; ++q) sw[wl][q][lane] = xt32[q * N + p];
-                    }
-                    __syncwarp();
-                    float part[NR];
-#pragma unroll
-                    for (int q = 0; q < NR; ++q) part[q] = 0.f;
-#pragma unroll 4
-                    for (int j = 0; j < nb; ++j) {
-                        const float4 v = sx[wl][j];
-                        const float dx = v.x - xa[0], dy = v.y - xa[1], dz = v.z - xa[2];
-                        const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                        const float f = KF<KIND>::f32(kp, r2);
-#pragma unroll
-                        for (int q = 0; q < NR; ++q) part[q] = fmaf(f, sw[wl][q][j], part[q]);
-                    }
-#pragma unroll
-                    for (int q = 0; q < NR; ++q) two_sum_add(s[q], c[q], part[q]);
-                }
-            }
-            if (act) {
-                const int64_t dst = perm[i0 + a];
-#pragma unroll
-                for (int q = 0; q < NR; ++q) {
-                    // the pair (i, i) was evaluated as K(0); the diagonal takes the configured value
-                    const double near = kp.s * ((double)s[q] + (double)c[q]) +
-                                        (kp.diag - kp.s * (double)k0) * (double)xt32[q * N + i0 + a];
-                    y[q * ld + dst] = (TO)(far[q] + near);
-                }
-            }
-        }
-    }
-}
-
 // ---- non-radial kernels (FP64 only): point-based evaluation -----------------
 template <int NR>
 __global__ void k_m2l_generic(KParams kp, int d, const int32_t *tgt, int64_t ntgt, const int32_t *il_off,
@@ -525,14 +768,59 @@ __global__ void k_leaf_generic(KParams kp, int d, const int32_t *leaves, int64_t
 }
 
 // ---- launch helpers ----------------------------------------------------------
+template <int KIND>
+void launch_m2l_f32(Handle *h, const float *w32, double *u) {
+    for (int ls = 0; ls < 5; ++ls) {
+        const int n = h->n_m2l_items[ls];
+        if (!n) continue;
+        const unsigned g = grid_for(n, MV_WARPS, 152 * 16);
+#define NNCA_M2L(LS)                                                                                                  \
+    k_m2l_f32<KIND, LS><<<g, 32 * MV_WARPS, 0, h->stream>>>(h->kp, h->m2l_items[ls], n, h->il_off, h->il_idx,          \
+                                                            h->prange, h->pv4, h->chi4, h->clo4, w32, w32 + h->npiv, u)
+        switch (ls) {
+        case 0: NNCA_M2L(0); break;
+        case 1: NNCA_M2L(1); break;
+        case 2: NNCA_M2L(2); break;
+        case 3: NNCA_M2L(3); break;
+        default: NNCA_M2L(4); break;
+        }
+#undef NNCA_M2L
+        NNCA_LAUNCH_CHECK();
+        ++h->launches;
+    }
+}
+
+template <int KIND, class TO>
+void launch_leaf_f32(Handle *h, const double *op, const double *u, const float *xt32, const double *xt64, TO *y) {
+    for (int ls = 0; ls < 5; ++ls) {
+        const int n = h->n_leaf_items[ls];
+        if (!n) continue;
+        const unsigned g = grid_for(n, MV_WARPS, 152 * 16);
+#define NNCA_LEAF(LS)                                                                                                  \
+    k_leaf_f32<KIND, LS, TO><<<g, 32 * MV_WARPS, 0, h->stream>>>(h->kp, h->leaf_items[ls], n, h->cbeg, h->cend,         \
+                                                                 h->nb_off, h->nb_idx, h->piv_off, h->op_off, op, u,    \
+                                                                 h->xh4, h->xl4, xt32, xt64, h->perm, y)
+        switch (ls) {
+        case 0: NNCA_LEAF(0); break;
+        case 1: NNCA_LEAF(1); break;
+        case 2: NNCA_LEAF(2); break;
+        case 3: NNCA_LEAF(3); break;
+        default: NNCA_LEAF(4); break;
+        }
+#undef NNCA_LEAF
+        NNCA_LAUNCH_CHECK();
+        ++h->launches;
+    }
+}
+
 void ensure_workspace(Handle *h, int64_t nrhs) {
     if (h->ws && h->ws_nrhs >= nrhs) return;
     if (h->ws) {
         dev_free(h, h->ws);
         h->ws = nullptr;
     }
-    // x in tree order (FP64 and FP32 copies), w and u (FP64)
-    const size_t bytes = (size_t)nrhs * ((h->n + 2 * h->npiv) * sizeof(double) + h->n * sizeof(float)) + 256;
+    // x in tree order (FP64 and FP32 copies), w (FP64 and FP32 hi + lo) and u (FP64)
+    const size_t bytes = (size_t)nrhs * ((h->n + 2 * h->npiv) * sizeof(double) + (h->n + 2 * h->npiv) * sizeof(float)) + 256;
     h->ws = dev_alloc(h, bytes);
     h->ws_bytes = bytes;
     h->ws_nrhs = nrhs;
@@ -542,11 +830,12 @@ void ensure_workspace(Handle *h, int64_t nrhs) {
 template <bool FP32, int NR, int KIND, class TO>
 void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
     cudaStream_t s = h->stream;
-    const int64_t N = h->n, npiv = h->npiv, nc = h->ncell;
+    const int64_t N = h->n, npiv = h->npiv;
     double *xt = (double *)h->ws;
     double *w = xt + NR * N;
     double *u = w + NR * npiv;
     float *xt32 = FP32 ? (float *)(u + NR * npiv) : nullptr;
+    float *w32 = FP32 ? xt32 + NR * N : nullptr;
     const TO *xin = (const TO *)x + r0 * ld;
     TO *yout = (TO *)y + r0 * ld;
     prof_mark(h, 0);
@@ -560,7 +849,7 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
         const int64_t lb = h->level_base[h->kappa], le = h->level_base[h->kappa + 1];
         k_upward<double, NR><<<grid_for((le - lb) * 32, 128), 128, 0, s>>>(lb, le, 1, h->cbeg, h->cend, h->cch_beg,
                                                                            h->cch_end, h->piv_off, h->op_off, op, xt,
-                                                                           N, w, npiv);
+                                                                           N, w, npiv, w32);
         NNCA_LAUNCH_CHECK();
         ++h->launches;
         for (int l = h->kappa - 1; l >= h->lmin; --l) {
@@ -568,20 +857,18 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
             ++h->launches;
             k_upward<double, NR><<<grid_for((b1 - b0) * 32, 128), 128, 0, s>>>(b0, b1, 0, h->cbeg, h->cend,
                                                                                h->cch_beg, h->cch_end, h->piv_off,
-                                                                               h->op_off, op, xt, N, w, npiv);
+                                                                               h->op_off, op, xt, N, w, npiv, w32);
             NNCA_LAUNCH_CHECK();
         }
         prof_mark(h, 2);
         if (h->n_m2l_tgt > 0) {
-            ++h->launches;
             const unsigned g = grid_for(h->n_m2l_tgt, MV_WARPS, 152 * 16);
+            if (!(FP32 && kernel_is_radial(h->kp.kind))) ++h->launches;
             if (!kernel_is_radial(h->kp.kind)) {
                 k_m2l_generic<NR><<<grid_for(h->n_m2l_tgt * 32, 128), 128, 0, s>>>(
                     h->kp, h->d, h->m2l_tgt, h->n_m2l_tgt, h->il_off, h->il_idx, h->piv_off, h->pv64, npiv, w, u);
             } else if (FP32) {
-                k_m2l_f32<KIND, NR><<<g, 32 * MV_WARPS, 0, s>>>(h->kp, h->d, h->m2l_tgt, h->n_m2l_tgt, h->il_off,
-                                                                h->il_idx, h->piv_off, h->pv32, npiv, h->ccen, nc, w,
-                                                                u);
+                launch_m2l_f32<KIND>(h, w32, u);
             } else {
                 k_m2l_f64<KIND, NR><<<g, 32 * MV_WARPS, 0, s>>>(h->kp, h->d, h->m2l_tgt, h->n_m2l_tgt, h->il_off,
                                                                 h->il_idx, h->piv_off, h->pv64, npiv, w, u);
@@ -602,16 +889,14 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
         prof_mark(h, 3);
     }
     prof_mark(h, 4);
-    ++h->launches;
+    if (!(FP32 && kernel_is_radial(h->kp.kind))) ++h->launches;
     const unsigned gl = grid_for(h->nleaf, MV_WARPS, 152 * 16);
     if (!kernel_is_radial(h->kp.kind)) {
         k_leaf_generic<NR, TO><<<grid_for(h->nleaf * 32, 128), 128, 0, s>>>(
             h->kp, h->d, h->leaf_order, h->nleaf, h->cbeg, h->cend, h->nb_off, h->nb_idx, h->piv_off, h->op_off, op, u,
             npiv, h->xs, N, xt, h->perm, yout, ld);
     } else if (FP32) {
-        k_leaf_f32<KIND, NR, TO><<<gl, 32 * MV_WARPS, 0, s>>>(h->kp, h->d, h->leaf_order, h->nleaf, h->cbeg, h->cend,
-                                                              h->nb_off, h->nb_idx, h->piv_off, h->op_off, op, u, npiv,
-                                                              h->xs32, N, h->ccen, nc, xt32, h->perm, yout, ld);
+        launch_leaf_f32<KIND, TO>(h, op, u, xt32, xt, yout);
     } else {
         k_leaf_f64<KIND, NR, TO><<<gl, 32 * MV_WARPS, 0, s>>>(h->kp, h->d, h->leaf_order, h->nleaf, h->cbeg, h->cend,
                                                               h->nb_off, h->nb_idx, h->piv_off, h->op_off, op, u, npiv,
@@ -625,7 +910,7 @@ template <bool FP32, int KIND, class TO>
 void run_all(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld) {
     int64_t r0 = 0;
     while (r0 < nrhs) {
-        if (nrhs - r0 >= 4) {
+        if (!FP32 && nrhs - r0 >= 4) {
             run_chunk<FP32, 4, KIND, TO>(h, x, y, ld, r0);
             r0 += 4;
         } else {

@@ -219,6 +219,8 @@ struct Handle {
 
     // product data (device)
     double *ccen = nullptr;       // [d][ncell] cell centres
+    float *ccen_hi = nullptr;     // [d][ncell] centre rounded to float
+    float *ccen_lo = nullptr;     // [d][ncell] centre - hi, rounded to float
     double *pv64 = nullptr;       // [d][npiv] pivot coordinates
     float *pv32 = nullptr;        // [d][npiv] pivot coordinates relative to their cell centre
     float *xs32 = nullptr;        // [d][n] point coordinates relative to their leaf centre
@@ -227,6 +229,15 @@ struct Handle {
     int64_t n_m2l_tgt = 0;
     int32_t *leaf_order = nullptr;  // leaves, heaviest near field first
     int64_t nleaf = 0;
+    // FP32 product: packed data and work items (cell, first target, count) per slice count 2^s
+    int2 *prange = nullptr;       // [ncell] (first pivot, rank)
+    float4 *pv4 = nullptr;        // [npiv] pivot coordinates relative to the cell centre
+    float4 *chi4 = nullptr, *clo4 = nullptr;   // [ncell] centre as float hi + lo
+    float4 *xh4 = nullptr, *xl4 = nullptr;     // [n] point coordinates as float hi + lo
+    int2 *m2l_items[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int n_m2l_items[5] = {0, 0, 0, 0, 0};
+    int2 *leaf_items[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int n_leaf_items[5] = {0, 0, 0, 0, 0};
 
     // product workspace
     void *ws = nullptr;
