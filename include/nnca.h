@@ -153,6 +153,24 @@ nnca_status nnca_matvec(nnca_handle h, const void *x, void *y, int64_t nrhs, int
 nnca_status nnca_matvec_host(nnca_handle h, const void *x_host, void *y_host, int64_t nrhs, int64_t ld,
                              int dtype, int precision, void *stream);
 
+/* The product for ONE right-hand side with no device allocation. The paper
+ * has no counterpart; this is a library service. nnca_matvec allocates its
+ * workspace with cudaMalloc on its first call; callers that cannot allocate
+ * then (a fixed device-memory budget already given to their own allocator, or
+ * latency-critical loops that cannot accept cudaMalloc's implicit device
+ * synchronisation) call this instead. The workspace comes from one file-scope
+ * device array of NNCA_NOALLOC_BYTES that every GPU loading the library holds
+ * until exit. Limit: (n + 2 * pivots) * 12 + 256 bytes must fit in it, else
+ * NNCA_ERR_INVALID_ARG with the sizes in nnca_last_error (pivots:
+ * nnca_stats.n_pivots). The first call on a device looks the array's address
+ * up (cudaGetSymbolAddress): make it before any stream capture. All calls share
+ * the array and it keeps the last call's contents; each call clears what must
+ * start at zero, and calls that overlap on the GPU race. Profiling must be off.
+ * x, y, ld, dtype, precision, stream: as for nnca_matvec with nrhs = 1. */
+#define NNCA_NOALLOC_BYTES (64u << 20)
+nnca_status nnca_matvec_noalloc(nnca_handle h, const void *x, void *y, int64_t ld, int dtype, int precision,
+                                void *stream);
+
 /* Free every device and host resource of the handle (NULL is a no-op).
  * Synchronises the device first. */
 void nnca_destroy(nnca_handle h);

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnnca.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "tree.cu", "lists.cu", "aca.cu", "matvec.cu", "scan.cu"]
+SOURCES = ["api.cu", "tree.cu", "lists.cu", "aca.cu", "matvec.cu", "scan.cu", "noalloc.cu"]
 HEADERS = ["nnca_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -8,8 +8,6 @@
 
 #include "nnca_internal.cuh"
 
-struct nnca_handle_s : nnca::Handle {};
-
 namespace nnca {
 
 static thread_local std::string g_last_error;

@@ -274,3 +274,6 @@ unsigned read_status(Handle *h);
 void prof_mark(Handle *h, int slot);
 
 }  // namespace nnca
+
+// The opaque handle of the C ABI is the library's Handle.
+struct nnca_handle_s : nnca::Handle {};

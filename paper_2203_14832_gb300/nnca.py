@@ -28,8 +28,8 @@ F64, F32 = 0, 1
 PREC_FP64, PREC_FP32 = 0, 1
 EXPORTS = ["PERM", "KEYS", "LEVEL_BASE", "CKEY", "CBEG", "CEND", "CPAR", "CCH_BEG", "CCH_END", "NB_OFF", "NB_IDX",
            "IL_OFF", "IL_IDX", "PIV_OFF", "PIV_ROW", "PIV_COL", "PASSTHRU", "CAND_OFF", "OP_OFF", "OP"]
-SYMBOLS = ["nnca_build", "nnca_matvec", "nnca_matvec_host", "nnca_destroy", "nnca_get_stats", "nnca_export",
-           "nnca_set_profiling", "nnca_last_error", "nnca_status_string"]
+SYMBOLS = ["nnca_build", "nnca_matvec", "nnca_matvec_host", "nnca_matvec_noalloc", "nnca_destroy", "nnca_get_stats",
+           "nnca_export", "nnca_set_profiling", "nnca_last_error", "nnca_status_string"]
 
 
 class NncaError(RuntimeError):
@@ -76,6 +76,8 @@ def lib() -> C.CDLL:
         L.nnca_get_stats.argtypes = [vp, C.POINTER(_Stats)]
         L.nnca_export.restype = C.c_int
         L.nnca_export.argtypes = [vp, C.c_int, vp, C.c_int64, C.POINTER(C.c_int64)]
+        L.nnca_matvec_noalloc.restype = C.c_int
+        L.nnca_matvec_noalloc.argtypes = [vp, vp, vp, C.c_int64, C.c_int, C.c_int, vp]
         L.nnca_set_profiling.restype = C.c_int
         L.nnca_set_profiling.argtypes = [vp, C.c_int]
         L.nnca_last_error.restype = C.c_char_p
@@ -139,6 +141,16 @@ def nnca_matvec(handle, x, y, nrhs: int, ld: int, precision: int = PREC_FP64, st
     dtype = F64 if x.dtype == torch.float64 else F32
     assert x.dtype == y.dtype and x.is_cuda and y.is_cuda
     _check(lib().nnca_matvec(handle, x.data_ptr(), y.data_ptr(), nrhs, ld, dtype, precision, _stream_ptr(stream)),
+           handle)
+
+
+def nnca_matvec_noalloc(handle, x, y, ld: int, precision: int = PREC_FP64, stream=None):
+    """y = A~ x for one right-hand side with no device allocation (workspace in a
+    fixed device array of the library; see include/nnca.h for the limit)."""
+    import torch
+    dtype = F64 if x.dtype == torch.float64 else F32
+    assert x.dtype == y.dtype and x.is_cuda and y.is_cuda
+    _check(lib().nnca_matvec_noalloc(handle, x.data_ptr(), y.data_ptr(), ld, dtype, precision, _stream_ptr(stream)),
            handle)
 
 
