@@ -160,7 +160,7 @@ nnca_status nnca_matvec_host(nnca_handle h, const void *x_host, void *y_host, in
  * latency-critical loops that cannot accept cudaMalloc's implicit device
  * synchronisation) call this instead. The workspace comes from one file-scope
  * device array of NNCA_NOALLOC_BYTES that every GPU loading the library holds
- * until exit. Limit: (n + 2 * pivots) * 12 + 256 bytes must fit in it, else
+ * until exit. Limit: 12 * n + 20 * pivots + 256 bytes must fit in it, else
  * NNCA_ERR_INVALID_ARG with the sizes in nnca_last_error (pivots:
  * nnca_stats.n_pivots). The first call on a device looks the array's address
  * up (cudaGetSymbolAddress): make it before any stream capture. All calls share

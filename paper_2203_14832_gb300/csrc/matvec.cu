@@ -161,12 +161,7 @@ __global__ void k_upward(int64_t b0, int64_t b1, int leaf, const int32_t *cbeg, 
 #pragma unroll
             for (int q = 0; q < NR; ++q) {
                 w[q * npiv + piv_off[B] + b] = acc[q];
-                if (w32) {
-                    // w = hi + lo in float: the M2L sums keep w to ~1e-14 relative
-                    const float hi = (float)acc[q];
-                    w32[q * npiv + piv_off[B] + b] = hi;
-                    w32[(q + NR) * npiv + piv_off[B] + b] = (float)((double)acc[q] - (double)hi);
-                }
+                if (w32) w32[q * npiv + piv_off[B] + b] = (float)acc[q];
             }
         }
     }
@@ -301,13 +296,23 @@ template <int KIND, bool SAFE> struct KF2 {
                        SAFE ? KF<KIND>::f32(kp, v.y) : KF<KIND>::f32_far(kp, v.y));
     }
 };
+// rsqrt of both halves of a packed pair, unpacked and repacked inside one PTX
+// block so that the halves can stay in their register pair
+__device__ __forceinline__ f2 f2_rsqrt(f2 a) {
+    f2 r;
+    asm("{\n\t.reg .f32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\trsqrt.approx.ftz.f32 lo, lo;\n\t"
+        "rsqrt.approx.ftz.f32 hi, hi;\n\tmov.b64 %0, {lo, hi};\n\t}"
+        : "=l"(r)
+        : "l"(a));
+    return r;
+}
+
 template <bool SAFE> struct KF2<NNCA_K_INV_R, SAFE> {
     // 1/r: one MUFU rsqrt (relative error ~1e-7). An optional Newton step
     // f <- f - (f/2)(r^2 f^2 - 1) takes it to float rounding, at 4 more packed
     // operations per pair; measured, it changes the product's error by ~3%.
     static __device__ __forceinline__ f2 eval(const KParams &, f2 r2) {
-        const float2 v = f2_unpack(r2);
-        f2 f = f2_pack(mufu_rsqrt(v.x), mufu_rsqrt(v.y));
+        f2 f = f2_rsqrt(r2);
 #if NNCA_RSQRT_NEWTON
         const f2 h = f2_mul(r2, f);
         const f2 e = f2_fma(h, f, f2_pack(-1.f, -1.f));
@@ -315,6 +320,7 @@ template <bool SAFE> struct KF2<NNCA_K_INV_R, SAFE> {
         f = f2_fma(hf, e, f);
 #endif
         if (SAFE) {
+            const float2 v = f2_unpack(r2);
             float2 g = f2_unpack(f);
             g.x = v.x > 0.f ? g.x : 0.f;
             g.y = v.y > 0.f ? g.y : 0.f;
@@ -335,10 +341,9 @@ template <bool SAFE> struct KF2<NNCA_K_INV_R, SAFE> {
 constexpr int RING = 64;
 constexpr float FAR_AWAY = 1.0e18f;
 
-// LO: near field, low parts of the coordinates in slots 2-3. !LO: far field,
-// low part of the weight in slot 2 ([wl0 wl1 - -]).
+// LO: near field, low parts of the coordinates in slots 2-3.
 template <bool LO> struct Ring2 {
-    float4 v[RING / 2][LO ? 4 : 3];
+    float4 v[RING / 2][LO ? 4 : 2];
 };
 
 template <int KIND, int LOGS, bool SAFE, bool LO>
@@ -360,15 +365,14 @@ struct Stream2 {
     }
     __device__ __forceinline__ void eval_chunk(const KParams &kp) {
         const int base = (done & (RING - 1)) >> 1;   // source-pair index of the chunk
-        f2 acc = 0ull, acc2 = 0ull;
+        // four short partial chains per lane (two sources each), combined pairwise
+        f2 acc[4] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll
         for (int i = 0; i < 16 / S; ++i) {
             const int q = base + s + S * i;
             const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(&R.v[q][0]);
             const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(&R.v[q][1]);
             f2 dx = f2_sub(A.x, tx), dy = f2_sub(A.y, ty), dz = f2_sub(B.x, tz);
-            f2 wlo = 0ull;
-            if (!LO) wlo = *reinterpret_cast<const f2 *>(&R.v[q][2]);
             if (LO) {
                 const ulonglong2 C = *reinterpret_cast<const ulonglong2 *>(&R.v[q][2]);
                 const ulonglong2 D = *reinterpret_cast<const ulonglong2 *>(&R.v[q][3]);
@@ -379,12 +383,9 @@ struct Stream2 {
             f2 r2 = f2_mul(dx, dx);
             r2 = f2_fma(dy, dy, r2);
             r2 = f2_fma(dz, dz, r2);
-            const f2 fv = KF2<KIND, SAFE>::eval(kp, r2);
-            if (i & 1) acc2 = f2_fma(fv, B.y, acc2);
-            else acc = f2_fma(fv, B.y, acc);
-            if (!LO) acc2 = f2_fma(fv, wlo, acc2);
+            acc[i & 3] = f2_fma(KF2<KIND, SAFE>::eval(kp, r2), B.y, acc[i & 3]);
         }
-        const float2 a = f2_unpack(f2_add(acc, acc2));
+        const float2 a = f2_unpack(f2_add(f2_add(acc[0], acc[1]), f2_add(acc[2], acc[3])));
         two_sum_add(sum, comp, a.x + a.y);
     }
     __device__ __forceinline__ void flush_full(const KParams &kp) {
@@ -410,8 +411,6 @@ struct Stream2 {
                 p[8 + h] = xl;
                 p[10 + h] = yl;
                 p[12 + h] = zl;
-            } else {
-                p[8 + h] = xl;   // far field: the low part of the weight
             }
         }
         fill += n;
@@ -446,7 +445,7 @@ __global__ void __launch_bounds__(32 * MV_WARPS) k_m2l_f32(KParams kp, const int
                                                           const int32_t *il_off, const int32_t *il_idx,
                                                           const int2 *prange, const float4 *pv4,
                                                           const float4 *chi, const float4 *clo, const float *w,
-                                                          const float *wlo, double *u) {
+                                                          double *u) {
     __shared__ __align__(16) Ring2<false> ring[MV_WARPS];
     constexpr int S = 1 << LOGS;
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
@@ -477,12 +476,11 @@ __global__ void __launch_bounds__(32 * MV_WARPS) k_m2l_f32(KParams kp, const int
             int k = 0, b0 = 0;
             int p0 = __shfl_sync(0xffffffffu, pk.x, 0), rY = __shfl_sync(0xffffffffu, pk.y, 0);
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            float wv = 0.f, wl = 0.f;
+            float wv = 0.f;
             int n = min(32, rY);
             if (lane < n) {
                 v = pv4[p0 + lane];
                 wv = w[p0 + lane];
-                wl = wlo[p0 + lane];
             }
             while (k < ne) {
                 const float sx = __shfl_sync(0xffffffffu, shx, k), sy = __shfl_sync(0xffffffffu, shy, k),
@@ -499,13 +497,12 @@ __global__ void __launch_bounds__(32 * MV_WARPS) k_m2l_f32(KParams kp, const int
                 }
                 const int n2 = k2 < ne ? min(32, r2n - b2) : 0;
                 float4 v2 = make_float4(0.f, 0.f, 0.f, 0.f);
-                float w2 = 0.f, wl2 = 0.f;
+                float w2 = 0.f;
                 if (lane < n2) {
                     v2 = pv4[p2 + b2 + lane];
                     w2 = w[p2 + b2 + lane];
-                    wl2 = wlo[p2 + b2 + lane];
                 }
-                if (n > 0) st.push(kp, lane, n, v.x + sx, v.y + sy, v.z + sz, wv, wl, 0.f, 0.f);
+                if (n > 0) st.push(kp, lane, n, v.x + sx, v.y + sy, v.z + sz, wv, 0.f, 0.f, 0.f);
                 k = k2;
                 b0 = b2;
                 p0 = p2;
@@ -513,7 +510,6 @@ __global__ void __launch_bounds__(32 * MV_WARPS) k_m2l_f32(KParams kp, const int
                 n = n2;
                 v = v2;
                 wv = w2;
-                wl = wl2;
             }
         }
         st.finish(kp, lane);
@@ -776,7 +772,7 @@ void launch_m2l_f32(Handle *h, const float *w32, double *u) {
         const unsigned g = grid_for(n, MV_WARPS, 152 * 16);
 #define NNCA_M2L(LS)                                                                                                  \
     k_m2l_f32<KIND, LS><<<g, 32 * MV_WARPS, 0, h->stream>>>(h->kp, h->m2l_items[ls], n, h->il_off, h->il_idx,          \
-                                                            h->prange, h->pv4, h->chi4, h->clo4, w32, w32 + h->npiv, u)
+                                                            h->prange, h->pv4, h->chi4, h->clo4, w32, u)
         switch (ls) {
         case 0: NNCA_M2L(0); break;
         case 1: NNCA_M2L(1); break;
@@ -819,8 +815,8 @@ void ensure_workspace(Handle *h, int64_t nrhs) {
         dev_free(h, h->ws);
         h->ws = nullptr;
     }
-    // x in tree order (FP64 and FP32 copies), w (FP64 and FP32 hi + lo) and u (FP64)
-    const size_t bytes = (size_t)nrhs * ((h->n + 2 * h->npiv) * sizeof(double) + (h->n + 2 * h->npiv) * sizeof(float)) + 256;
+    // x in tree order (FP64 and FP32 copies), w (FP64 and FP32) and u (FP64)
+    const size_t bytes = (size_t)nrhs * ((h->n + 2 * h->npiv) * sizeof(double) + (h->n + h->npiv) * sizeof(float)) + 256;
     h->ws = dev_alloc(h, bytes);
     h->ws_bytes = bytes;
     h->ws_nrhs = nrhs;

@@ -68,12 +68,12 @@ extern "C" nnca_status nnca_matvec_noalloc(nnca_handle hh, const void *x, void *
         return NNCA_ERR_INVALID_ARG;
     }
     // the workspace of one right-hand side: x in tree order (double and float),
-    // w and u (double), w as float hi + lo
-    const size_t need = (size_t)(h->n + 2 * h->npiv) * sizeof(double) + (size_t)(h->n + 2 * h->npiv) * sizeof(float) + 256;
+    // w and u (double), w (float)
+    const size_t need = (size_t)(h->n + 2 * h->npiv) * sizeof(double) + (size_t)(h->n + h->npiv) * sizeof(float) + 256;
     if (need > kScratchBytes) {
         h->last_error = "nnca_matvec_noalloc: the problem needs " + std::to_string(need) +
                         " bytes of workspace, more than the fixed " + std::to_string(kScratchBytes) +
-                        " (n + 2 * pivots must stay below about " + std::to_string(kScratchBytes / 12) + ")";
+                        " (12 * n + 20 * pivots + 256 bytes)";
         return NNCA_ERR_INVALID_ARG;
     }
     void *scratch = nullptr;
