@@ -124,6 +124,11 @@ typedef struct {
     double pass_ms[8];
     int64_t pass_calls;            /* products summed in pass_ms                   */
     int64_t launches_per_product;  /* kernels of this library in the last product  */
+    int64_t device_status;         /* device-side check bits since the build (read
+                                      by nnca_get_stats): 2 an index failed a bounds
+                                      check, 16 a bounded wait on an asynchronous
+                                      copy ran out; the product's result is then
+                                      not valid. 1 (ACA scratch retried) is benign. */
 } nnca_stats;
 
 /* Build the H^2 representation of A(i, j) = K(p_i, q_j).

@@ -832,6 +832,78 @@ __global__ void k_pack_points(int64_t n, int64_t npiv, int d, const double *xs, 
     }
 }
 
+// Sources of every cell for the FP32 M2L, in pairs [x0 x1 y0 y1][z0 z1 w0 w1]
+// relative to the cell centre; padding sources far away; weights 0 (each
+// product writes its own). One warp per cell.
+__global__ void k_pack_sources(int64_t nc, const int2 *prange, const int32_t *spk_off, const float4 *pv4,
+                               float4 *spk) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < nc; c += nw) {
+        const int2 pr = prange[c];
+        const int64_t q0 = spk_off[c], nq = spk_off[c + 1] - q0;
+        for (int64_t q = lane; q < nq; q += 32) {
+            const float4 far4 = make_float4(FAR_AWAY, FAR_AWAY, FAR_AWAY, 0.f);
+            const float4 v0 = 2 * q < pr.y ? pv4[pr.x + 2 * q] : far4;
+            const float4 v1 = 2 * q + 1 < pr.y ? pv4[pr.x + 2 * q + 1] : far4;
+            spk[2 * (q0 + q)] = make_float4(v0.x, v1.x, v0.y, v1.y);
+            spk[2 * (q0 + q) + 1] = make_float4(v0.z, v1.z, 0.f, 0.f);
+        }
+    }
+}
+
+// Staging plan of the FP32 M2L for parent P (Table 1): the children Y of N(P)
+// with sources, each with the mask of P's children that admit it (the test of
+// the list construction, so the mask bit of child X is set exactly when Y is
+// in IL(X)), cut greedily into rounds of at most M2L_STAGE_RECS cells and
+// M2L_STAGE_CAP padded sources. PASS 0 counts the records, PASS 1 writes them.
+template <int PASS>
+__global__ void k_m2l_plan(int64_t np, const int32_t *parents, int d, int num, int den, const int32_t *ccoord,
+                           int64_t ncell, const int32_t *cch_beg, const int32_t *cch_end, const int32_t *nb_off,
+                           const int32_t *nb_idx, const int2 *prange, const int32_t *spk_off, const int64_t *rec_off,
+                           int64_t *rec_cnt, int4 *rec) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+        const int P = parents[i];
+        const int cb = cch_beg[P], nch = cch_end[P] - cb;
+        int4 *out = PASS ? rec + rec_off[i] : nullptr;
+        int64_t n = 0, first = 0;
+        int used = 0, nr = 0;
+        for (int q = nb_off[P]; q < nb_off[P + 1]; ++q) {
+            const int Q = nb_idx[q];
+            for (int y = cch_beg[Q]; y < cch_end[Q]; ++y) {
+                const int rank = prange[y].y;
+                if (rank == 0) continue;
+                int mask = 0;
+                for (int c = 0; c < nch; ++c) {
+                    int64_t g2 = 0;
+                    for (int k = 0; k < d; ++k) {
+                        int64_t t = (int64_t)ccoord[(int64_t)k * ncell + y] - ccoord[(int64_t)k * ncell + cb + c];
+                        if (t < 0) t = -t;
+                        t -= 1;
+                        if (t < 0) t = 0;
+                        g2 += t * t;
+                    }
+                    if ((int64_t)d * den <= (int64_t)num * g2) mask |= 1 << c;
+                }
+                if (!mask) continue;
+                const int npad = m2l_padded(rank);
+                if (nr == M2L_STAGE_RECS || used + npad > M2L_STAGE_CAP) {
+                    if (PASS) out[first].w = nr;
+                    first = n;
+                    used = 0;
+                    nr = 0;
+                }
+                if (PASS) out[n] = make_int4(y, spk_off[y], (used >> 1) | ((npad >> 1) << 11) | (mask << 22), 0);
+                used += npad;
+                ++nr;
+                ++n;
+            }
+        }
+        if (PASS && nr > 0) out[first].w = nr;
+        if (!PASS) rec_cnt[i] = n;
+    }
+}
+
 // work counts: m2l pairs per target cell, p2p pairs per leaf
 __global__ void k_work_counts(int64_t b0, int64_t b1, int64_t leaf0, const int32_t *il_off, const int32_t *il_idx,
                               const int32_t *nb_off, const int32_t *nb_idx, const int32_t *piv_off,
@@ -975,9 +1047,10 @@ void build_finish(Handle *h) {
     h->stats.m2l_pairs = (int64_t)ht[0];
     h->stats.p2p_pairs = (int64_t)ht[1];
 
-    // FP32 product: packed arrays and work items. A cell's targets form items of
-    // 32; the remainder c < 32 gets S = 2^s lanes per target (c * S <= 32, S <= 16),
-    // which split its sources. Items are ordered heaviest first.
+    // FP32 product: packed arrays and work items. Near field: a leaf's targets
+    // form items of 32; the remainder c < 32 gets S = 2^s lanes per target
+    // (c * S <= 32, S <= 16), which split its sources. Items are ordered
+    // heaviest first.
     h->prange = dalloc<int2>(h, nc);
     h->chi4 = dalloc<float4>(h, nc);
     h->clo4 = dalloc<float4>(h, nc);
@@ -1020,16 +1093,91 @@ void build_finish(Handle *h) {
         }
     };
     {
-        std::vector<int32_t> cells;
-        std::vector<int64_t> count, weight;
-        for (int64_t c = 0; c < nc; ++c)
-            if (hw[c] > 0) {
-                const int64_t r = hpo[c + 1] - hpo[c];
-                cells.push_back((int32_t)c);
-                count.push_back(r);
-                weight.push_back(hw[c] / std::max<int64_t>(r, 1));
+        // FP32 M2L sources, packed per cell
+        std::vector<int32_t> hso(nc + 1, 0);
+        int64_t npairs = 0;
+        h->m2l_fp32_unsupported = nullptr;
+        for (int64_t c = 0; c < nc; ++c) {
+            if (hpo[c + 1] - hpo[c] > M2L_STAGE_CAP)
+                h->m2l_fp32_unsupported = "the FP32 product supports ranks up to 512 (use FP64)";
+            npairs += m2l_padded(hpo[c + 1] - hpo[c]) / 2;
+            NNCA_REQUIRE(npairs < (1ll << 30), NNCA_ERR_UNSUPPORTED, "too many pivots for the FP32 M2L");
+            hso[c + 1] = (int32_t)npairs;
+        }
+        h->n_spk_pairs = npairs;
+        h->spk_off = dalloc<int32_t>(h, nc + 1);
+        NNCA_CUDA(cudaMemcpy(h->spk_off, hso.data(), (nc + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+        h->spk = dalloc<float4>(h, 2 * (size_t)npairs);
+        k_pack_sources<<<grid_for(nc * 32, 256), 256, 0, s>>>(nc, h->prange, h->spk_off, h->pv4, h->spk);
+        NNCA_LAUNCH_CHECK();
+
+        // M2L items: the targets of one parent's children (their pivots are
+        // contiguous) in items of at most M2L_GROUP_TARGETS, split at multiples of
+        // M2L_WARP_TARGETS; one staging plan per parent
+        std::vector<int32_t> hchb(nc), hche(nc);
+        NNCA_CUDA(cudaMemcpy(hchb.data(), h->cch_beg, nc * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        NNCA_CUDA(cudaMemcpy(hche.data(), h->cch_end, nc * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        struct Group { int64_t weight; int parent_slot, t0, nt; };
+        std::vector<Group> groups;
+        std::vector<int32_t> parents;
+        const int64_t pl0 = h->lmin >= 1 ? h->level_base[h->lmin - 1] : 0;
+        const int64_t pl1 = h->level_base[kappa];
+        for (int64_t P = pl0; P < pl1 && h->lmin <= kappa; ++P) {
+            const int32_t c0 = hchb[P], c1 = hche[P];
+            if (c1 <= c0) continue;
+            int64_t work = 0;
+            for (int32_t c = c0; c < c1; ++c) work += hw[c];
+            const int64_t T = hpo[c1] - hpo[c0];
+            if (work == 0 || T == 0) continue;
+            if (T >= 65536) {
+                h->m2l_fp32_unsupported = "the FP32 product supports up to 65535 pivots per group of siblings (use FP64)";
+                continue;
             }
-        make_items(cells, count, weight, h->m2l_items, h->n_m2l_items);
+            const int slot = (int)parents.size();
+            parents.push_back((int32_t)P);
+            const int64_t WT = M2L_WARP_TARGETS;
+            const int64_t nw = (T + WT - 1) / WT, k = (nw + M2L_GROUP_WARPS - 1) / M2L_GROUP_WARPS;
+            for (int64_t i = 0; i < k; ++i) {
+                const int64_t t0 = WT * (i * nw / k), t1 = std::min<int64_t>(T, WT * ((i + 1) * nw / k));
+                groups.push_back({work * (t1 - t0) / T, slot, (int)t0, (int)(t1 - t0)});
+            }
+        }
+        std::stable_sort(groups.begin(), groups.end(), [](const Group &x, const Group &y) { return x.weight > y.weight; });
+        const int64_t np = (int64_t)parents.size();
+        std::vector<int64_t> roff(np + 1, 0);
+        h->n_m2l_plan = 0;
+        if (np > 0 && !h->m2l_fp32_unsupported) {
+            int32_t *dpar = scr.get<int32_t>(np);
+            int64_t *dcnt = scr.get<int64_t>(np), *doff = scr.get<int64_t>(np);
+            NNCA_CUDA(cudaMemcpy(dpar, parents.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice));
+            k_m2l_plan<0><<<grid_for(np, 128), 128, 0, s>>>(np, dpar, d, h->cfg.eta2_num, h->cfg.eta2_den, h->ccoord, nc,
+                                                           h->cch_beg, h->cch_end, h->nb_off, h->nb_idx, h->prange,
+                                                           h->spk_off, nullptr, dcnt, nullptr);
+            NNCA_LAUNCH_CHECK();
+            std::vector<int64_t> hcnt(np);
+            NNCA_CUDA(cudaMemcpy(hcnt.data(), dcnt, np * sizeof(int64_t), cudaMemcpyDeviceToHost));
+            for (int64_t i = 0; i < np; ++i) roff[i + 1] = roff[i] + hcnt[i];
+            NNCA_REQUIRE(roff[np] < (1ll << 31), NNCA_ERR_UNSUPPORTED, "FP32 M2L plan exceeds 2^31 records");
+            h->n_m2l_plan = roff[np];
+            h->m2l_plan = dalloc<int4>(h, roff[np]);
+            NNCA_CUDA(cudaMemcpy(doff, roff.data(), np * sizeof(int64_t), cudaMemcpyHostToDevice));
+            k_m2l_plan<1><<<grid_for(np, 128), 128, 0, s>>>(np, dpar, d, h->cfg.eta2_num, h->cfg.eta2_den, h->ccoord, nc,
+                                                           h->cch_beg, h->cch_end, h->nb_off, h->nb_idx, h->prange,
+                                                           h->spk_off, doff, nullptr, h->m2l_plan);
+            NNCA_LAUNCH_CHECK();
+        }
+        std::vector<int4> v;
+        for (auto &g : groups) {
+            const int P = parents[g.parent_slot];
+            v.push_back(make_int4(P, g.t0 | (g.nt << 16), (int)roff[g.parent_slot],
+                                  (int)(roff[g.parent_slot + 1] - roff[g.parent_slot])));
+        }
+        h->n_m2l_groups = (int)v.size();
+        h->m2l_groups = dalloc<int4>(h, v.size());
+        h->m2l_next = dalloc<int>(h, 1);
+        if (!v.empty())
+            NNCA_CUDA(cudaMemcpy(h->m2l_groups, v.data(), v.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        NNCA_CUDA(cudaStreamSynchronize(s));
     }
     {
         std::vector<int32_t> cells;

@@ -273,6 +273,8 @@ nnca_status nnca_matvec_host(nnca_handle h, const void *x_host, void *y_host, in
         matvec(h, xd, yd, nrhs, h->n, dtype, precision);
         NNCA_CUDA(cudaMemcpy2DAsync(y_host, ld * es, yd, h->n * es, h->n * es, nrhs, cudaMemcpyDeviceToHost, s));
         NNCA_CUDA(cudaStreamSynchronize(s));
+        NNCA_REQUIRE(!(read_status(h) & (DEV_WAIT_TIMEOUT | DEV_BAD_INDEX)), NNCA_ERR_INTERNAL,
+                     "nnca_matvec_host: a device-side check of the product failed");
     } catch (const Error &e) {
         return fail(h, e.status, e.what());
     } catch (const std::exception &e) {
@@ -291,6 +293,7 @@ nnca_status nnca_get_stats(nnca_handle h, nnca_stats *out) {
     if (!h || !out) return fail(h, NNCA_ERR_INVALID_ARG, "nnca_get_stats: NULL argument");
     try {
         prof_flush(h);
+        h->stats.device_status = read_status(h);
     } catch (const Error &e) {
         return fail(h, e.status, e.what());
     }

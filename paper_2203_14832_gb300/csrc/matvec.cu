@@ -130,7 +130,8 @@ __global__ void k_perm_in(const TI *x, int64_t ld, int64_t N, int64_t nrhs, cons
 template <class T, int NR>
 __global__ void k_upward(int64_t b0, int64_t b1, int leaf, const int32_t *cbeg, const int32_t *cend,
                          const int32_t *cch_beg, const int32_t *cch_end, const int32_t *piv_off, const int64_t *op_off,
-                         const T *op, const T *xt, int64_t N, T *w, int64_t npiv, float *w32) {
+                         const T *op, const T *xt, int64_t N, T *w, int64_t npiv, float *spk_w,
+                         const int32_t *spk_off) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -159,10 +160,9 @@ __global__ void k_upward(int64_t b0, int64_t b1, int leaf, const int32_t *cbeg, 
                 for (int q = 0; q < NR; ++q) acc[q] += c * src[q * ld + a];
             }
 #pragma unroll
-            for (int q = 0; q < NR; ++q) {
-                w[q * npiv + piv_off[B] + b] = acc[q];
-                if (w32) w32[q * npiv + piv_off[B] + b] = (float)acc[q];
-            }
+            for (int q = 0; q < NR; ++q) w[q * npiv + piv_off[B] + b] = acc[q];
+            // FP32 product: the weight slot of pivot b in the packed sources
+            if (spk_w) spk_w[((int64_t)spk_off[B] + (b >> 1)) * 8 + 6 + (b & 1)] = (float)acc[0];
         }
     }
 }
@@ -339,7 +339,6 @@ template <bool SAFE> struct KF2<NNCA_K_INV_R, SAFE> {
 // sources of weight 0. A work item is up to 32/S targets of one cell; each
 // target is served by S lanes that split every chunk's sources between them.
 constexpr int RING = 64;
-constexpr float FAR_AWAY = 1.0e18f;
 
 // LO: near field, low parts of the coordinates in slots 2-3.
 template <bool LO> struct Ring2 {
@@ -439,83 +438,245 @@ __device__ __forceinline__ void unpack_item(int2 it, int &cell, int &a0, int &c)
     c = (it.y >> 16) & 0xff;
 }
 
-// ---- M2L, FP32 evaluation -----------------------------------------------------
-template <int KIND, int LOGS>
-__global__ void __launch_bounds__(32 * MV_WARPS) k_m2l_f32(KParams kp, const int2 *items, int nitems,
-                                                          const int32_t *il_off, const int32_t *il_idx,
-                                                          const int2 *prange, const float4 *pv4,
-                                                          const float4 *chi, const float4 *clo, const float *w,
-                                                          double *u) {
-    __shared__ __align__(16) Ring2<false> ring[MV_WARPS];
-    constexpr int S = 1 << LOGS;
-    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    const int t = lane >> LOGS, s = lane & (S - 1);
-    for (int it = blockIdx.x * MV_WARPS + wl; it < nitems; it += gridDim.x * MV_WARPS) {
-        int X, a0, c;
-        unpack_item(items[it], X, a0, c);
-        const int2 pr = prange[X];
-        const bool act = t < c;
-        const float4 xa = act ? pv4[pr.x + a0 + t] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 hX = chi[X], lX = clo[X];
-        Stream2<KIND, LOGS, false, false> st(ring[wl], s, xa.x, xa.y, xa.z, 0.f, 0.f, 0.f);
-        const int e1 = il_off[X + 1];
-        for (int e0 = il_off[X]; e0 < e1; e0 += 32) {
-            // headers of up to 32 interaction-list cells, one per lane
-            const int ne = min(32, e1 - e0);
-            int2 pk = make_int2(0, 0);
-            float shx = 0.f, shy = 0.f, shz = 0.f;
-            if (lane < ne) {
-                const int Y = il_idx[e0 + lane];
-                pk = prange[Y];
-                const float4 hY = chi[Y], lY = clo[Y];
-                shx = (hY.x - hX.x) + (lY.x - lX.x);
-                shy = (hY.y - hX.y) + (lY.y - lX.y);
-                shz = (hY.z - hX.z) + (lY.z - lX.z);
-            }
-            // walk the chunks of 32 sources, loading the next chunk before pushing the current
-            int k = 0, b0 = 0;
-            int p0 = __shfl_sync(0xffffffffu, pk.x, 0), rY = __shfl_sync(0xffffffffu, pk.y, 0);
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            float wv = 0.f;
-            int n = min(32, rY);
-            if (lane < n) {
-                v = pv4[p0 + lane];
-                wv = w[p0 + lane];
-            }
-            while (k < ne) {
-                const float sx = __shfl_sync(0xffffffffu, shx, k), sy = __shfl_sync(0xffffffffu, shy, k),
-                            sz = __shfl_sync(0xffffffffu, shz, k);
-                // next chunk
-                int k2 = k, b2 = b0 + 32;
-                if (b2 >= rY) { k2 = k + 1; b2 = 0; }
-                int p2 = p0, r2n = rY;
-                if (k2 != k && k2 < ne) {
-                    p2 = __shfl_sync(0xffffffffu, pk.x, k2);
-                    r2n = __shfl_sync(0xffffffffu, pk.y, k2);
-                } else if (k2 != k) {
-                    r2n = 0;
-                }
-                const int n2 = k2 < ne ? min(32, r2n - b2) : 0;
-                float4 v2 = make_float4(0.f, 0.f, 0.f, 0.f);
-                float w2 = 0.f;
-                if (lane < n2) {
-                    v2 = pv4[p2 + b2 + lane];
-                    w2 = w[p2 + b2 + lane];
-                }
-                if (n > 0) st.push(kp, lane, n, v.x + sx, v.y + sy, v.z + sz, wv, 0.f, 0.f, 0.f);
-                k = k2;
-                b0 = b2;
-                p0 = p2;
-                rY = r2n;
-                n = n2;
-                v = v2;
-                wv = w2;
-            }
-        }
-        st.finish(kp, lane);
-        const double r = st.result();
-        if (act && s == 0) u[pr.x + a0 + t] = kp.s * r;
+// ---- M2L, FP32 evaluation: one thread block per group of sibling cells -------------
+// The children X of one parent P draw their interaction lists from one set, the
+// children of N(P): IL(X) is its part that is admissible for X (Table 1). A
+// block serves up to M2L_GROUP_TARGETS targets (pivots) of P's children, two
+// consecutive ones per lane, in their order (so a warp spans few children).
+// P's staging plan lists the children of N(P) with sources, each with the
+// mask of P's children that admit it, in rounds. Warp 0 stages a round with
+// one bulk asynchronous copy (TMA) per cell from the packed sources into one of
+// M2L_STAGE_BUFS shared buffers, tracked by a "full" mbarrier, up to
+// M2L_STAGE_AHEAD rounds ahead of its own evaluation; the warps release each
+// buffer on its "empty" mbarrier, so a warp may run a round behind the others
+// without stalling the staging. Blocks take items from a counter, heaviest
+// first. A
+// warp evaluates a staged cell when it is admissible for the child of one of
+// its targets: the targets move into the cell's frame (c_Y - c_P subtracted
+// once per cell), sum the cell in float, and add the partial into their
+// compensated total only when their own child admits the cell. Every wait is
+// bounded (about 2^31 clocks); one that runs out sets DEV_WAIT_TIMEOUT.
+constexpr int M2L_GROUP_THREADS = 32 * M2L_GROUP_WARPS;
+
+constexpr int M2L_STAGE_AHEAD = M2L_STAGE_BUFS - 2;
+
+struct M2lGroupSmem {
+    float4 src[M2L_STAGE_BUFS][M2L_STAGE_CAP / 2][2];   // staged source pairs
+    int hdr[M2L_STAGE_BUFS][M2L_STAGE_RECS];            // staging slot | pairs << 11 | child mask << 22
+    float4 sh[M2L_STAGE_BUFS][M2L_STAGE_RECS];          // centre of the cell minus centre of P
+    int nrec[M2L_STAGE_BUFS];
+    unsigned long long full[M2L_STAGE_BUFS], empty[M2L_STAGE_BUFS];   // mbarriers
+    int2 ch_range[8];                                   // pivots of P's children
+    int item;
+    int abort;
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(void *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(void *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(void *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// wait until the phase of the given parity has completed; false after about 2^31 clocks
+__device__ __forceinline__ bool mbar_wait(void *bar, unsigned parity) {
+    const unsigned a = smem_addr(bar);
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > (1ll << 31)) return false;
     }
+}
+// bulk copy global -> shared (16-byte aligned, size a multiple of 16), completing on bar
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, void *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Warp 0: stage the round of plan records that starts at k into buffer b, for
+// its use-th use (after the warps have released its previous use). Returns the
+// first record of the next round, or kend after a timed-out wait.
+__device__ __forceinline__ int m2l_stage(M2lGroupSmem &S, int b, unsigned use, const int4 *plan, int k, int kend,
+                                         const float4 *spk, const float4 *chi, const float4 *clo, float4 hP,
+                                         float4 lP, unsigned *status) {
+    const int lane = threadIdx.x & 31;
+    if (use > 0 && !mbar_wait(&S.empty[b], (use - 1) & 1)) {
+        if (lane == 0) {
+            atomicOr(status, DEV_WAIT_TIMEOUT);
+            *(volatile int *)&S.abort = 1;
+        }
+        return kend;
+    }
+    int4 r = make_int4(0, 0, 0, 0);
+    if (k + lane < kend) r = plan[k + lane];
+    const int nrec = __shfl_sync(0xffffffffu, r.w, 0);   // cells in this round (first record)
+    if (nrec < 1 || nrec > M2L_STAGE_RECS || k + nrec > kend) {   // a malformed plan: stop, never spin
+        if (lane == 0) {
+            atomicOr(status, DEV_BAD_INDEX);
+            *(volatile int *)&S.abort = 1;
+        }
+        return kend;
+    }
+    unsigned bytes = 0;
+    if (lane < nrec) {
+        S.hdr[b][lane] = r.z;
+        const float4 hY = chi[r.x], lY = clo[r.x];
+        S.sh[b][lane] = make_float4((hY.x - hP.x) + (lY.x - lP.x), (hY.y - hP.y) + (lY.y - lP.y),
+                                    (hY.z - hP.z) + (lY.z - lP.z), 0.f);
+        bytes = (unsigned)((r.z >> 11) & 0x7ff) * 32u;
+    }
+    const unsigned total = __reduce_add_sync(0xffffffffu, bytes);
+    if (lane == 0) S.nrec[b] = nrec;
+    __syncwarp();
+    if (lane == 0) mbar_arrive_tx(&S.full[b], total);
+    __syncwarp();
+    if (lane < nrec) bulk_g2s(&S.src[b][r.z & 0x7ff][0], spk + 2 * (int64_t)r.y, bytes, &S.full[b]);
+    return k + nrec;
+}
+
+// one target of a lane: child slot (31: none), pivot, coordinates in P's frame, sum
+struct GroupTarget {
+    int c = 31;
+    int g = 0;
+    f2 tx = 0ull, ty = 0ull, tz = 0ull;   // (t, t) packed
+    float sum = 0.f, comp = 0.f;
+};
+
+__device__ __forceinline__ void group_target(GroupTarget &T, bool act, int g, int nch, int cb, const int2 *ch_range,
+                                             const float4 *pv4, const float4 *chi, const float4 *clo, float4 hP,
+                                             float4 lP) {
+    T.g = g;
+    if (!act) return;
+    int c = 0;
+    for (int k = 1; k < nch; ++k)
+        if (ch_range[k].x <= g) c = k;
+    T.c = c;
+    const int X = cb + c;
+    const float4 v = pv4[g], hX = chi[X], lX = clo[X];
+    const float tx = v.x + ((hX.x - hP.x) + (lX.x - lP.x));
+    const float ty = v.y + ((hX.y - hP.y) + (lX.y - lP.y));
+    const float tz = v.z + ((hX.z - hP.z) + (lX.z - lP.z));
+    T.tx = f2_pack(tx, tx);
+    T.ty = f2_pack(ty, ty);
+    T.tz = f2_pack(tz, tz);
+}
+
+// acc += f(|s - t|^2) w over a packed pair of sources
+template <int KIND>
+__device__ __forceinline__ f2 group_pair(const KParams &kp, const ulonglong2 &A, const ulonglong2 &B, f2 tx, f2 ty,
+                                         f2 tz, f2 acc) {
+    const f2 dx = f2_sub(A.x, tx), dy = f2_sub(A.y, ty), dz = f2_sub(B.x, tz);
+    f2 r2 = f2_mul(dx, dx);
+    r2 = f2_fma(dy, dy, r2);
+    r2 = f2_fma(dz, dz, r2);
+    return f2_fma(KF2<KIND, false>::eval(kp, r2), B.y, acc);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group(KParams kp, const int4 *items, int nitems,
+                                                               int *next_item, const int4 *plan,
+                                                               const int32_t *cch_beg, const int32_t *cch_end,
+                                                               const int2 *prange, const float4 *pv4,
+                                                               const float4 *chi, const float4 *clo,
+                                                               const float4 *spk, double *u, unsigned *status) {
+    __shared__ __align__(128) M2lGroupSmem S;
+    const int tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
+    if (tid == 0) {
+        for (int b = 0; b < M2L_STAGE_BUFS; ++b) {
+            mbar_init(&S.full[b], 1);
+            mbar_init(&S.empty[b], M2L_GROUP_WARPS);
+        }
+        S.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    unsigned R = 0, Rp = 0;   // rounds consumed by every warp; rounds staged (warp 0)
+    for (;;) {
+        __syncthreads();   // the previous item is done with the shared state
+        if (tid == 0) S.item = atomicAdd(next_item, 1);
+        __syncthreads();
+        const int it = S.item;
+        if (it >= nitems || *(volatile int *)&S.abort) break;
+        const int4 item = items[it];
+        const int P = item.x, t0 = item.y & 0xffff, nt = item.y >> 16, kend = item.z + item.w;
+        const int cb = cch_beg[P], nch = cch_end[P] - cb;
+        if (tid < nch) S.ch_range[tid] = prange[cb + tid];
+        __syncthreads();
+        const float4 hP = chi[P], lP = clo[P];
+        int kprod = item.z, kcons = item.z;
+        // this lane's two targets: pivots g and g + 1 of P's children
+        const int j = t0 + wl * M2L_WARP_TARGETS + 2 * lane, jend = t0 + nt;
+        const int g = S.ch_range[0].x + j;
+        GroupTarget Ta, Tb;
+        group_target(Ta, j < jend, g, nch, cb, S.ch_range, pv4, chi, clo, hP, lP);
+        group_target(Tb, j + 1 < jend, g + 1, nch, cb, S.ch_range, pv4, chi, clo, hP, lP);
+        const unsigned omask =
+            __reduce_or_sync(0xffffffffu, (Ta.c < 31 ? 1u << Ta.c : 0u) | (Tb.c < 31 ? 1u << Tb.c : 0u));
+        while (kcons < kend) {
+            // warp 0 keeps up to M2L_STAGE_AHEAD rounds staged beyond the one it evaluates
+            if (wl == 0)
+                while (kprod < kend && Rp <= R + M2L_STAGE_AHEAD) {
+                    kprod = m2l_stage(S, Rp % M2L_STAGE_BUFS, Rp / M2L_STAGE_BUFS, plan, kprod, kend, spk, chi, clo,
+                                      hP, lP, status);
+                    ++Rp;
+                }
+            const int b = R % M2L_STAGE_BUFS;
+            if (!mbar_wait(&S.full[b], (R / M2L_STAGE_BUFS) & 1)) {
+                if (lane == 0) {
+                    atomicOr(status, DEV_WAIT_TIMEOUT);
+                    *(volatile int *)&S.abort = 1;
+                }
+                break;
+            }
+            const int nrec = S.nrec[b];
+            if (nrec < 1) break;   // unreachable with a well-formed plan
+            if (omask) {
+                for (int i = 0; i < nrec; ++i) {
+                    const int hw = S.hdr[b][i];
+                    const unsigned m = ((unsigned)hw >> 22) & omask;
+                    if (!m) continue;
+                    const float4 sh = S.sh[b][i];
+                    const f2 SX = f2_pack(sh.x, sh.x), SY = f2_pack(sh.y, sh.y), SZ = f2_pack(sh.z, sh.z);
+                    const f2 xa = f2_sub(Ta.tx, SX), ya = f2_sub(Ta.ty, SY), za = f2_sub(Ta.tz, SZ);
+                    const f2 xb = f2_sub(Tb.tx, SX), yb = f2_sub(Tb.ty, SY), zb = f2_sub(Tb.tz, SZ);
+                    const int q0 = hw & 0x7ff, q1 = q0 + ((hw >> 11) & 0x7ff);
+                    f2 a0 = 0ull, a1 = 0ull, b0 = 0ull, b1 = 0ull;
+                    for (int q = q0; q < q1; q += 2) {
+                        const ulonglong2 A0 = *reinterpret_cast<const ulonglong2 *>(&S.src[b][q][0]);
+                        const ulonglong2 B0 = *reinterpret_cast<const ulonglong2 *>(&S.src[b][q][1]);
+                        const ulonglong2 A1 = *reinterpret_cast<const ulonglong2 *>(&S.src[b][q + 1][0]);
+                        const ulonglong2 B1 = *reinterpret_cast<const ulonglong2 *>(&S.src[b][q + 1][1]);
+                        a0 = group_pair<KIND>(kp, A0, B0, xa, ya, za, a0);
+                        b0 = group_pair<KIND>(kp, A0, B0, xb, yb, zb, b0);
+                        a1 = group_pair<KIND>(kp, A1, B1, xa, ya, za, a1);
+                        b1 = group_pair<KIND>(kp, A1, B1, xb, yb, zb, b1);
+                    }
+                    const float2 pa = f2_unpack(f2_add(a0, a1)), pb = f2_unpack(f2_add(b0, b1));
+                    if ((m >> Ta.c) & 1u) two_sum_add(Ta.sum, Ta.comp, pa.x + pa.y);
+                    if ((m >> Tb.c) & 1u) two_sum_add(Tb.sum, Tb.comp, pb.x + pb.y);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.empty[b]);
+            ++R;
+            kcons += nrec;
+        }
+        if (Ta.c < 31) u[Ta.g] = kp.s * ((double)Ta.sum + (double)Ta.comp);
+        if (Tb.c < 31) u[Tb.g] = kp.s * ((double)Tb.sum + (double)Tb.comp);
+    }
+    // after a timed-out wait: let copies still in flight land before the block exits
+    if (tid == 0)
+        for (unsigned r = R; r < Rp; ++r) mbar_wait(&S.full[r % M2L_STAGE_BUFS], (r / M2L_STAGE_BUFS) & 1);
 }
 
 // ---- leaves: L2P (FP64) + P2P (FP32 evaluation on hi/lo coordinates) ------------
@@ -765,25 +926,19 @@ __global__ void k_leaf_generic(KParams kp, int d, const int32_t *leaves, int64_t
 
 // ---- launch helpers ----------------------------------------------------------
 template <int KIND>
-void launch_m2l_f32(Handle *h, const float *w32, double *u) {
-    for (int ls = 0; ls < 5; ++ls) {
-        const int n = h->n_m2l_items[ls];
-        if (!n) continue;
-        const unsigned g = grid_for(n, MV_WARPS, 152 * 16);
-#define NNCA_M2L(LS)                                                                                                  \
-    k_m2l_f32<KIND, LS><<<g, 32 * MV_WARPS, 0, h->stream>>>(h->kp, h->m2l_items[ls], n, h->il_off, h->il_idx,          \
-                                                            h->prange, h->pv4, h->chi4, h->clo4, w32, u)
-        switch (ls) {
-        case 0: NNCA_M2L(0); break;
-        case 1: NNCA_M2L(1); break;
-        case 2: NNCA_M2L(2); break;
-        case 3: NNCA_M2L(3); break;
-        default: NNCA_M2L(4); break;
-        }
-#undef NNCA_M2L
-        NNCA_LAUNCH_CHECK();
-        ++h->launches;
-    }
+void launch_m2l_f32(Handle *h, double *u) {
+    if (!h->n_m2l_groups) return;
+    int dev = 0, nsm = 152, per_sm = 1;
+    NNCA_CUDA(cudaGetDevice(&dev));
+    NNCA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    NNCA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_m2l_group<KIND>, M2L_GROUP_THREADS, 0));
+    const unsigned g = (unsigned)std::min<int64_t>(h->n_m2l_groups, (int64_t)nsm * std::max(1, per_sm));
+    NNCA_CUDA(cudaMemsetAsync(h->m2l_next, 0, sizeof(int), h->stream));
+    k_m2l_group<KIND><<<g, M2L_GROUP_THREADS, 0, h->stream>>>(h->kp, h->m2l_groups, h->n_m2l_groups, h->m2l_next,
+                                                             h->m2l_plan, h->cch_beg, h->cch_end, h->prange, h->pv4,
+                                                             h->chi4, h->clo4, h->spk, u, h->dev_status);
+    NNCA_LAUNCH_CHECK();
+    ++h->launches;
 }
 
 template <int KIND, class TO>
@@ -831,7 +986,8 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
     double *w = xt + NR * N;
     double *u = w + NR * npiv;
     float *xt32 = FP32 ? (float *)(u + NR * npiv) : nullptr;
-    float *w32 = FP32 ? xt32 + NR * N : nullptr;
+    // FP32: the weights go straight into the packed M2L sources
+    float *spk_w = FP32 && kernel_is_radial(h->kp.kind) ? reinterpret_cast<float *>(h->spk) : nullptr;
     const TO *xin = (const TO *)x + r0 * ld;
     TO *yout = (TO *)y + r0 * ld;
     prof_mark(h, 0);
@@ -845,7 +1001,7 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
         const int64_t lb = h->level_base[h->kappa], le = h->level_base[h->kappa + 1];
         k_upward<double, NR><<<grid_for((le - lb) * 32, 128), 128, 0, s>>>(lb, le, 1, h->cbeg, h->cend, h->cch_beg,
                                                                            h->cch_end, h->piv_off, h->op_off, op, xt,
-                                                                           N, w, npiv, w32);
+                                                                           N, w, npiv, spk_w, h->spk_off);
         NNCA_LAUNCH_CHECK();
         ++h->launches;
         for (int l = h->kappa - 1; l >= h->lmin; --l) {
@@ -853,7 +1009,8 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
             ++h->launches;
             k_upward<double, NR><<<grid_for((b1 - b0) * 32, 128), 128, 0, s>>>(b0, b1, 0, h->cbeg, h->cend,
                                                                                h->cch_beg, h->cch_end, h->piv_off,
-                                                                               h->op_off, op, xt, N, w, npiv, w32);
+                                                                               h->op_off, op, xt, N, w, npiv, spk_w,
+                                                                               h->spk_off);
             NNCA_LAUNCH_CHECK();
         }
         prof_mark(h, 2);
@@ -864,7 +1021,7 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
                 k_m2l_generic<NR><<<grid_for(h->n_m2l_tgt * 32, 128), 128, 0, s>>>(
                     h->kp, h->d, h->m2l_tgt, h->n_m2l_tgt, h->il_off, h->il_idx, h->piv_off, h->pv64, npiv, w, u);
             } else if (FP32) {
-                launch_m2l_f32<KIND>(h, w32, u);
+                launch_m2l_f32<KIND>(h, u);
             } else {
                 k_m2l_f64<KIND, NR><<<g, 32 * MV_WARPS, 0, s>>>(h->kp, h->d, h->m2l_tgt, h->n_m2l_tgt, h->il_off,
                                                                 h->il_idx, h->piv_off, h->pv64, npiv, w, u);
@@ -937,6 +1094,8 @@ void matvec(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int dty
                  "non-radial kernels support only the FP64 product");
     NNCA_REQUIRE(h->d <= 3 || precision == NNCA_PREC_FP64, NNCA_ERR_UNSUPPORTED,
                  "the FP32 product supports d <= 3");
+    NNCA_REQUIRE(!h->m2l_fp32_unsupported || precision == NNCA_PREC_FP64, NNCA_ERR_UNSUPPORTED,
+                 h->m2l_fp32_unsupported ? h->m2l_fp32_unsupported : "");
     ensure_workspace(h, std::min<int64_t>(nrhs, 4));
     h->launches = 0;
     if (precision == NNCA_PREC_FP32) {

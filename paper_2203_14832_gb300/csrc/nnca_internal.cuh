@@ -44,7 +44,8 @@ enum : unsigned {
     DEV_POOL_EXHAUSTED = 1u,   // a cell ran out of ACA scratch: it is retried
     DEV_BAD_INDEX = 2u,        // an index failed a bounds check
     DEV_ZERO_PIVOT = 4u,       // the LU of a pivot block met an exact zero pivot
-    DEV_LIST_OVERFLOW = 8u
+    DEV_LIST_OVERFLOW = 8u,
+    DEV_WAIT_TIMEOUT = 16u     // a bounded wait on an asynchronous copy ran out
 };
 
 inline unsigned ceil_div(unsigned long long a, unsigned long long b) { return (unsigned)((a + b - 1) / b); }
@@ -159,6 +160,22 @@ __device__ __forceinline__ float kern32_r2(const KParams &kp, float r2) {
 
 inline bool kernel_is_radial(int kind) { return kind != NNCA_K_SEPARABLE && kind != NNCA_K_POLY2; }
 
+// The FP32 M2L runs one thread block of M2L_GROUP_WARPS warps per group of
+// sibling target cells, M2L_WARP_TARGETS consecutive targets per warp (two per
+// lane); a group item holds at most M2L_GROUP_TARGETS targets. Source cells
+// arrive in staging rounds of at most M2L_STAGE_RECS cells and M2L_STAGE_CAP
+// sources (padded counts), which bounds the largest rank it takes.
+constexpr int M2L_GROUP_WARPS = 4;
+constexpr int M2L_WARP_TARGETS = 64;
+constexpr int M2L_GROUP_TARGETS = M2L_WARP_TARGETS * M2L_GROUP_WARPS;
+constexpr int M2L_STAGE_CAP = 512;
+constexpr int M2L_STAGE_RECS = 32;
+constexpr int M2L_STAGE_BUFS = 4;
+// coordinate of a padding source: far from every target, weight 0
+constexpr float FAR_AWAY = 1.0e18f;
+// sources of a cell padded to a multiple of four (two packed pairs)
+__host__ __device__ inline int m2l_padded(int rank) { return (rank + 3) & ~3; }
+
 // ---------------------------------------------------------------------------
 // Handle.
 struct Handle;
@@ -234,8 +251,21 @@ struct Handle {
     float4 *pv4 = nullptr;        // [npiv] pivot coordinates relative to the cell centre
     float4 *chi4 = nullptr, *clo4 = nullptr;   // [ncell] centre as float hi + lo
     float4 *xh4 = nullptr, *xl4 = nullptr;     // [n] point coordinates as float hi + lo
-    int2 *m2l_items[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    int n_m2l_items[5] = {0, 0, 0, 0, 0};
+    // FP32 M2L: items (parent, first target | targets << 16, first plan record,
+    // plan records), heaviest first; plan records (cell, first source pair,
+    // staging slot | pairs << 11 | child mask << 22, cells in the round or 0);
+    // sources of every cell as pairs [x0 x1 y0 y1][z0 z1 w0 w1] relative to the
+    // cell centre, padded to m2l_padded(rank) with far-away sources of weight 0
+    // (the products write the weights w), from pair spk_off[cell]
+    int4 *m2l_groups = nullptr;
+    int n_m2l_groups = 0;
+    int *m2l_next = nullptr;      // item counter of the FP32 M2L launch
+    const char *m2l_fp32_unsupported = nullptr;   // why the FP32 M2L cannot run, or null
+    int4 *m2l_plan = nullptr;
+    int64_t n_m2l_plan = 0;
+    float4 *spk = nullptr;
+    int32_t *spk_off = nullptr;   // [ncell + 1]
+    int64_t n_spk_pairs = 0;
     int2 *leaf_items[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int n_leaf_items[5] = {0, 0, 0, 0, 0};
 

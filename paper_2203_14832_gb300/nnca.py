@@ -50,7 +50,8 @@ class _Stats(C.Structure):
                 ("n_pivots", C.c_int64), ("max_rank", C.c_int64), ("n_passthru", C.c_int64),
                 ("p2p_pairs", C.c_int64), ("m2l_pairs", C.c_int64), ("op_entries", C.c_int64),
                 ("device_bytes", C.c_int64), ("build_ms", C.c_double * 8), ("aca_retries", C.c_int64),
-                ("pass_ms", C.c_double * 8), ("pass_calls", C.c_int64), ("launches_per_product", C.c_int64)]
+                ("pass_ms", C.c_double * 8), ("pass_calls", C.c_int64), ("launches_per_product", C.c_int64),
+                ("device_status", C.c_int64)]
 
 
 _lib = None

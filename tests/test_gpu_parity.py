@@ -104,6 +104,7 @@ def test_full_parity(gpu, orc, wl, n, kw, tol32):
     assert rel(y32, yo) < tol32
     st = g.stats()
     assert st["kappa"] == o.kappa and st["lmin"] == o.lmin and st["ncell"] == o.ncell
+    assert st["device_status"] & (2 | 16) == 0   # no failed bounds check, no timed-out wait
     g.close()
 
 
@@ -132,8 +133,25 @@ def test_dimensions(gpu, orc, d, n, nu):
     check_structure(g, o)
     check_pivots(g, o)
     yo = o.matvec(x)
-    y = g.matvec(torch.as_tensor(x, device="cuda")).cpu().numpy()
+    xd = torch.as_tensor(x, device="cuda")
+    y = g.matvec(xd).cpu().numpy()
     assert rel(y, yo) < 1e-12
+    g.close()
+
+
+@pytest.mark.parametrize("d,n,nu", [(1, 3000, 8), (2, 5000, 20)])
+def test_fp32_low_dimensions(gpu, orc, d, n, nu):
+    """FP32 evaluations in 1D and 2D (1/r): within 1e-6 of the oracle's product."""
+    import torch
+    P = W.uniform_cube(n, d, 100 + d)
+    x = W.vector_normal(n, 200 + d)
+    kw = dict(d=d, leaf_size=nu, aca_tol=1e-7, kernel=W.K_INV_R, kparam=(1.0, 0, 0, 0))
+    g = gpu.H2(torch.as_tensor(P, device="cuda"), gpu.Config(**kw))
+    o = orc.H2(P, orc.Config(**kw))
+    yo = o.matvec(x)
+    y32 = g.matvec(torch.as_tensor(x, device="cuda"), gpu.PREC_FP32).cpu().numpy()
+    assert rel(y32, yo) < 1e-6
+    assert g.stats()["device_status"] & (2 | 16) == 0
     g.close()
 
 
