@@ -126,72 +126,161 @@ __global__ void k_perm_in(const TI *x, int64_t ld, int64_t N, int64_t nrhs, cons
     }
 }
 
-// ---- P2M / M2M: w_B[b] = sum_a op_B[a][b] * src[a] (one warp per cell) -------
-template <class T, int NR>
-__global__ void k_upward(int64_t b0, int64_t b1, int leaf, const int32_t *cbeg, const int32_t *cend,
-                         const int32_t *cch_beg, const int32_t *cch_end, const int32_t *piv_off, const int64_t *op_off,
-                         const T *op, const T *xt, int64_t N, T *w, int64_t npiv, float *spk_w,
-                         const int32_t *spk_off) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t B = b0 + warp; B < b1; B += nw) {
-        const int64_t r = piv_off[B + 1] - piv_off[B];
-        if (r == 0) continue;
-        const T *src;
-        int64_t m, ld;
-        if (leaf) {
-            src = xt + cbeg[B];
-            m = cend[B] - cbeg[B];
-            ld = N;
-        } else {
-            src = w + piv_off[cch_beg[B]];
-            m = piv_off[cch_end[B]] - piv_off[cch_beg[B]];
-            ld = npiv;
+// ---- P2M / M2M and L2L: batched small products with the FP64 operators --------
+// The operators of the upper levels are few and large (hundreds of rows), those
+// of the leaves many and small, so a team of TW warps serves one cell and each
+// lane keeps UP_BATCH independent loads of the operator in flight. The vector
+// the operator multiplies is staged in shared memory in chunks of UP_CHUNK.
+constexpr int UP_THREADS = 256;
+constexpr int UP_BATCH = 8;
+constexpr int UP_CHUNK = 512;
+
+// w_B[b] = sum_a op_B[a][b] src[a]; op_B is m x r, row-major (m: the points of a
+// leaf or the pivots of the children). The TW warps of a team split the rows;
+// the lanes take 32 columns at a time (coalesced row segments).
+template <class T, int NR, int TW>
+__global__ void __launch_bounds__(UP_THREADS) k_upward(int64_t b0, int64_t b1, int leaf, const int32_t *cbeg,
+                                                      const int32_t *cend, const int32_t *cch_beg,
+                                                      const int32_t *cch_end, const int32_t *piv_off,
+                                                      const int64_t *op_off, const T *op, const T *xt, int64_t N,
+                                                      T *w, int64_t npiv, float *spk_w, const int32_t *spk_off) {
+    constexpr int TEAMS = UP_THREADS / (32 * TW);
+    constexpr int CH = TW == 1 ? 64 : UP_CHUNK;   // rows staged per chunk
+    __shared__ T sv[TEAMS][NR][CH];
+    __shared__ T part[TEAMS][TW][NR][32];
+    const int lane = threadIdx.x & 31, tw = (threadIdx.x >> 5) % TW, team = threadIdx.x / (32 * TW);
+    const int tt = threadIdx.x % (32 * TW);   // thread within the team
+    for (int64_t B0 = b0 + (int64_t)blockIdx.x * TEAMS; B0 < b1; B0 += (int64_t)gridDim.x * TEAMS) {
+        const int64_t B = B0 + team;
+        const bool live = B < b1;
+        int64_t r = 0, m = 0, ld = 0;
+        const T *src = nullptr;
+        if (live) {
+            r = piv_off[B + 1] - piv_off[B];
+            if (leaf) {
+                src = xt + cbeg[B];
+                m = cend[B] - cbeg[B];
+                ld = N;
+            } else {
+                src = w + piv_off[cch_beg[B]];
+                m = piv_off[cch_end[B]] - piv_off[cch_beg[B]];
+                ld = npiv;
+            }
         }
-        const T *A = op + op_off[B];
-        for (int64_t b = lane; b < r; b += 32) {
+        const T *A = live ? op + op_off[B] : nullptr;
+        // the loops below run the same trip counts in every team of the block
+        int64_t mmax = m, rmax = r;
+        if (TEAMS > 1) {
+            __shared__ int64_t mr[TEAMS][2];
+            if (tt == 0) {
+                mr[team][0] = m;
+                mr[team][1] = r;
+            }
+            __syncthreads();
+            for (int k = 0; k < TEAMS; ++k) {
+                mmax = mr[k][0] > mmax ? mr[k][0] : mmax;
+                rmax = mr[k][1] > rmax ? mr[k][1] : rmax;
+            }
+        }
+        for (int64_t c0 = 0; c0 < rmax; c0 += 32) {
+            const int64_t b = c0 + lane;
             T acc[NR];
 #pragma unroll
             for (int q = 0; q < NR; ++q) acc[q] = 0;
-            for (int64_t a = 0; a < m; ++a) {
-                const T c = A[a * r + b];
+            for (int64_t a0 = 0; a0 < mmax; a0 += CH) {
+                const int64_t na = m - a0 < CH ? (m - a0 > 0 ? m - a0 : 0) : CH;
+                __syncthreads();
+                for (int64_t i = tt; i < na; i += 32 * TW)
 #pragma unroll
-                for (int q = 0; q < NR; ++q) acc[q] += c * src[q * ld + a];
+                    for (int q = 0; q < NR; ++q) sv[team][q][i] = src[q * ld + a0 + i];
+                __syncthreads();
+                if (b < r) {
+                    int64_t a = tw;
+                    for (; a + (UP_BATCH - 1) * TW < na; a += UP_BATCH * TW) {
+                        T c[UP_BATCH];
+#pragma unroll
+                        for (int k = 0; k < UP_BATCH; ++k) c[k] = A[(a0 + a + k * TW) * r + b];
+#pragma unroll
+                        for (int k = 0; k < UP_BATCH; ++k)
+#pragma unroll
+                            for (int q = 0; q < NR; ++q) acc[q] += c[k] * sv[team][q][a + k * TW];
+                    }
+                    for (; a < na; a += TW)
+#pragma unroll
+                        for (int q = 0; q < NR; ++q) acc[q] += A[(a0 + a) * r + b] * sv[team][q][a];
+                }
             }
+            if (TW > 1) {
 #pragma unroll
-            for (int q = 0; q < NR; ++q) w[q * npiv + piv_off[B] + b] = acc[q];
-            // FP32 product: the weight slot of pivot b in the packed sources
-            if (spk_w) spk_w[((int64_t)spk_off[B] + (b >> 1)) * 8 + 6 + (b & 1)] = (float)acc[0];
+                for (int q = 0; q < NR; ++q) part[team][tw][q][lane] = acc[q];
+                __syncthreads();
+                if (tw == 0)
+#pragma unroll
+                    for (int q = 0; q < NR; ++q) {
+                        T v = part[team][0][q][lane];
+#pragma unroll
+                        for (int k = 1; k < TW; ++k) v += part[team][k][q][lane];
+                        acc[q] = v;
+                    }
+            }
+            if (tw == 0 && b < r) {
+#pragma unroll
+                for (int q = 0; q < NR; ++q) w[q * npiv + piv_off[B] + b] = acc[q];
+                // FP32 product: the weight slot of pivot b in the packed sources
+                if (spk_w) spk_w[((int64_t)spk_off[B] + (b >> 1)) * 8 + 6 + (b & 1)] = (float)acc[0];
+            }
         }
     }
 }
 
-// ---- L2L: u_B[a] += sum_b op_P[row0 + a][b] * u_P[b] (one warp per cell) ----
+// u_{B_c} += C_{B_c P} u_P for the children of P: P's transfer C is m x r_P,
+// row-major, one row per pivot of P's children (in order). A block serves one
+// parent; its warps take rows 32 at a time, one row per lane, with u_P staged
+// in shared memory and UP_BATCH operator loads in flight per lane.
 template <class T, int NR>
-__global__ void k_l2l(int64_t b0, int64_t b1, const int32_t *cpar, const int32_t *cch_beg, const int32_t *piv_off,
-                      const int64_t *op_off, const T *op, T *u, int64_t npiv) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t B = b0 + warp; B < b1; B += nw) {
-        const int64_t P = cpar[B];
-        const int64_t rB = piv_off[B + 1] - piv_off[B], rP = piv_off[P + 1] - piv_off[P];
-        if (rB == 0 || rP == 0) continue;
-        const int64_t row0 = piv_off[B] - piv_off[cch_beg[P]];
-        const T *C = op + op_off[P] + row0 * rP;
-        const T *uP = u + piv_off[P];
-        for (int64_t a = lane; a < rB; a += 32) {
+__global__ void __launch_bounds__(UP_THREADS) k_l2l(int64_t p0, int64_t p1, const int32_t *cch_beg,
+                                                   const int32_t *cch_end, const int32_t *piv_off,
+                                                   const int64_t *op_off, const T *op, T *u, int64_t npiv) {
+    __shared__ T su[NR][UP_CHUNK];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    constexpr int W = UP_THREADS / 32;
+    for (int64_t P = p0 + blockIdx.x; P < p1; P += gridDim.x) {
+        const int64_t rP = piv_off[P + 1] - piv_off[P];
+        if (rP == 0 || cch_end[P] <= cch_beg[P]) continue;
+        const int64_t row0 = piv_off[cch_beg[P]], m = piv_off[cch_end[P]] - row0;
+        const T *C = op + op_off[P];
+        for (int64_t a0 = 0; a0 < m; a0 += 32 * W) {
+            const int64_t a = a0 + wl * 32 + lane;
             T acc[NR];
 #pragma unroll
             for (int q = 0; q < NR; ++q) acc[q] = 0;
-            for (int64_t b = 0; b < rP; ++b) {
-                const T c = C[a * rP + b];
+            for (int64_t c0 = 0; c0 < rP; c0 += UP_CHUNK) {
+                const int64_t nc = rP - c0 < UP_CHUNK ? rP - c0 : UP_CHUNK;
+                __syncthreads();
+                for (int64_t i = threadIdx.x; i < nc; i += UP_THREADS)
 #pragma unroll
-                for (int q = 0; q < NR; ++q) acc[q] += c * uP[q * npiv + b];
+                    for (int q = 0; q < NR; ++q) su[q][i] = u[q * npiv + piv_off[P] + c0 + i];
+                __syncthreads();
+                if (a < m) {
+                    const T *row = C + a * rP + c0;
+                    int64_t b = 0;
+                    for (; b + UP_BATCH <= nc; b += UP_BATCH) {
+                        T c[UP_BATCH];
+#pragma unroll
+                        for (int k = 0; k < UP_BATCH; ++k) c[k] = row[b + k];
+#pragma unroll
+                        for (int k = 0; k < UP_BATCH; ++k)
+#pragma unroll
+                            for (int q = 0; q < NR; ++q) acc[q] += c[k] * su[q][b + k];
+                    }
+                    for (; b < nc; ++b)
+#pragma unroll
+                        for (int q = 0; q < NR; ++q) acc[q] += row[b] * su[q][b];
+                }
             }
+            if (a < m)
 #pragma unroll
-            for (int q = 0; q < NR; ++q) u[q * npiv + piv_off[B] + a] += acc[q];
+                for (int q = 0; q < NR; ++q) u[q * npiv + row0 + a] += acc[q];
         }
     }
 }
@@ -999,7 +1088,7 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
     if (npiv > 0) NNCA_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * NR * npiv, s));
     if (h->lmin <= h->kappa && npiv > 0) {
         const int64_t lb = h->level_base[h->kappa], le = h->level_base[h->kappa + 1];
-        k_upward<double, NR><<<grid_for((le - lb) * 32, 128), 128, 0, s>>>(lb, le, 1, h->cbeg, h->cend, h->cch_beg,
+        k_upward<double, NR, 1><<<grid_for(le - lb, UP_THREADS / 32), UP_THREADS, 0, s>>>(lb, le, 1, h->cbeg, h->cend, h->cch_beg,
                                                                            h->cch_end, h->piv_off, h->op_off, op, xt,
                                                                            N, w, npiv, spk_w, h->spk_off);
         NNCA_LAUNCH_CHECK();
@@ -1007,7 +1096,7 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
         for (int l = h->kappa - 1; l >= h->lmin; --l) {
             const int64_t b0 = h->level_base[l], b1 = h->level_base[l + 1];
             ++h->launches;
-            k_upward<double, NR><<<grid_for((b1 - b0) * 32, 128), 128, 0, s>>>(b0, b1, 0, h->cbeg, h->cend,
+            k_upward<double, NR, UP_THREADS / 32><<<grid_for(b1 - b0, 1), UP_THREADS, 0, s>>>(b0, b1, 0, h->cbeg, h->cend,
                                                                                h->cch_beg, h->cch_end, h->piv_off,
                                                                                h->op_off, op, xt, N, w, npiv, spk_w,
                                                                                h->spk_off);
@@ -1030,10 +1119,11 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
         }
         prof_mark(h, 3);
         for (int l = h->lmin + 1; l <= h->kappa; ++l) {
-            const int64_t b0 = h->level_base[l], b1 = h->level_base[l + 1];
+            // parents at level l - 1 push down to their children at level l
+            const int64_t p0 = h->level_base[l - 1], p1 = h->level_base[l];
             ++h->launches;
-            k_l2l<double, NR><<<grid_for((b1 - b0) * 32, 128), 128, 0, s>>>(b0, b1, h->cpar, h->cch_beg, h->piv_off,
-                                                                            h->op_off, op, u, npiv);
+            k_l2l<double, NR><<<grid_for(p1 - p0, 1), UP_THREADS, 0, s>>>(p0, p1, h->cch_beg, h->cch_end, h->piv_off,
+                                                                             h->op_off, op, u, npiv);
             NNCA_LAUNCH_CHECK();
         }
     }
