@@ -860,8 +860,8 @@ __global__ void k_pack_sources(int64_t nc, const int2 *prange, const int32_t *sp
 template <int PASS>
 __global__ void k_m2l_plan(int64_t np, const int32_t *parents, int d, int num, int den, const int32_t *ccoord,
                            int64_t ncell, const int32_t *cch_beg, const int32_t *cch_end, const int32_t *nb_off,
-                           const int32_t *nb_idx, const int2 *prange, const int32_t *spk_off, const int64_t *rec_off,
-                           int64_t *rec_cnt, int4 *rec) {
+                           const int32_t *nb_idx, const int2 *prange, const int32_t *spk_off, const double *ccen,
+                           const int64_t *rec_off, int64_t *rec_cnt, int4 *rec, float4 *rec_sh) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
         const int P = parents[i];
         const int cb = cch_beg[P], nch = cch_end[P] - cb;
@@ -893,7 +893,13 @@ __global__ void k_m2l_plan(int64_t np, const int32_t *parents, int d, int num, i
                     used = 0;
                     nr = 0;
                 }
-                if (PASS) out[n] = make_int4(y, spk_off[y], (used >> 1) | ((npad >> 1) << 11) | (mask << 22), 0);
+                if (PASS) {
+                    out[n] = make_int4(y, spk_off[y], (used >> 1) | ((npad >> 1) << 11) | (mask << 22), 0);
+                    // c_Y - c_P, the FP64 difference rounded once
+                    float sh[3] = {0.f, 0.f, 0.f};
+                    for (int k = 0; k < d && k < 3; ++k) sh[k] = (float)(ccen[(int64_t)k * ncell + y] - ccen[(int64_t)k * ncell + P]);
+                    rec_sh[rec_off[i] + n] = make_float4(sh[0], sh[1], sh[2], 0.f);
+                }
                 used += npad;
                 ++nr;
                 ++n;
@@ -901,6 +907,59 @@ __global__ void k_m2l_plan(int64_t np, const int32_t *parents, int d, int num, i
         }
         if (PASS && nr > 0) out[first].w = nr;
         if (!PASS) rec_cnt[i] = n;
+    }
+}
+
+// Points of every leaf for the FP32 near field, in pairs
+// [xh0 xh1 yh0 yh1][zh0 zh1 w0 w1][xl0 xl1 yl0 yl1][zl0 zl1 0 0]; padding points
+// far away with weight 0; weights 0 (each product writes its own). One warp per leaf.
+__global__ void k_pack_near(int64_t l0, int64_t l1, const int32_t *cbeg, const int32_t *cend, const int32_t *ppk_off,
+                            const float4 *xh4, const float4 *xl4, float4 *ppk) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = l0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); c < l1; c += nw) {
+        const int64_t i0 = cbeg[c], n = cend[c] - i0;
+        const int64_t q0 = ppk_off[c], nq = ppk_off[c + 1] - q0;
+        for (int64_t q = lane; q < nq; q += 32) {
+            const float4 farh = make_float4(FAR_AWAY, FAR_AWAY, FAR_AWAY, 0.f), zero = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 h0 = 2 * q < n ? xh4[i0 + 2 * q] : farh, h1 = 2 * q + 1 < n ? xh4[i0 + 2 * q + 1] : farh;
+            const float4 o0 = 2 * q < n ? xl4[i0 + 2 * q] : zero, o1 = 2 * q + 1 < n ? xl4[i0 + 2 * q + 1] : zero;
+            float4 *dst = ppk + 4 * (q0 + q);
+            dst[0] = make_float4(h0.x, h1.x, h0.y, h1.y);
+            dst[1] = make_float4(h0.z, h1.z, 0.f, 0.f);
+            dst[2] = make_float4(o0.x, o1.x, o0.y, o1.y);
+            dst[3] = make_float4(o0.z, o1.z, 0.f, 0.f);
+        }
+    }
+}
+
+// Staging plan of the FP32 near field for leaf X: the leaves Y of N(X) (Table 1),
+// with a flag for X itself, cut greedily into rounds of at most NEAR_RECS cells
+// and NEAR_CAP point pairs. PASS 0 counts the records, PASS 1 writes them.
+template <int PASS>
+__global__ void k_near_plan(int64_t l0, int64_t l1, const int32_t *nb_off, const int32_t *nb_idx,
+                            const int32_t *ppk_off, const int64_t *rec_off, int64_t *rec_cnt, int4 *rec) {
+    for (int64_t X = l0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; X < l1; X += (int64_t)gridDim.x * blockDim.x) {
+        int4 *out = PASS ? rec + rec_off[X - l0] : nullptr;
+        int64_t n = 0, first = 0;
+        int used = 0, nr = 0;
+        for (int q = nb_off[X]; q < nb_off[X + 1]; ++q) {
+            const int Y = nb_idx[q];
+            const int np = ppk_off[Y + 1] - ppk_off[Y];
+            if (np == 0) continue;
+            if (nr == NEAR_RECS || used + np > NEAR_CAP) {
+                if (PASS) out[first].w = nr;
+                first = n;
+                used = 0;
+                nr = 0;
+            }
+            if (PASS) out[n] = make_int4(Y, ppk_off[Y], used | (np << 11) | ((Y == X ? 1 : 0) << 22), 0);
+            used += np;
+            ++nr;
+            ++n;
+        }
+        if (PASS && nr > 0) out[first].w = nr;
+        if (!PASS) rec_cnt[X - l0] = n;
     }
 }
 
@@ -1152,7 +1211,7 @@ void build_finish(Handle *h) {
             NNCA_CUDA(cudaMemcpy(dpar, parents.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice));
             k_m2l_plan<0><<<grid_for(np, 128), 128, 0, s>>>(np, dpar, d, h->cfg.eta2_num, h->cfg.eta2_den, h->ccoord, nc,
                                                            h->cch_beg, h->cch_end, h->nb_off, h->nb_idx, h->prange,
-                                                           h->spk_off, nullptr, dcnt, nullptr);
+                                                           h->spk_off, h->ccen, nullptr, dcnt, nullptr, nullptr);
             NNCA_LAUNCH_CHECK();
             std::vector<int64_t> hcnt(np);
             NNCA_CUDA(cudaMemcpy(hcnt.data(), dcnt, np * sizeof(int64_t), cudaMemcpyDeviceToHost));
@@ -1160,10 +1219,12 @@ void build_finish(Handle *h) {
             NNCA_REQUIRE(roff[np] < (1ll << 31), NNCA_ERR_UNSUPPORTED, "FP32 M2L plan exceeds 2^31 records");
             h->n_m2l_plan = roff[np];
             h->m2l_plan = dalloc<int4>(h, roff[np]);
+            h->m2l_plan_sh = dalloc<float4>(h, roff[np]);
             NNCA_CUDA(cudaMemcpy(doff, roff.data(), np * sizeof(int64_t), cudaMemcpyHostToDevice));
             k_m2l_plan<1><<<grid_for(np, 128), 128, 0, s>>>(np, dpar, d, h->cfg.eta2_num, h->cfg.eta2_den, h->ccoord, nc,
                                                            h->cch_beg, h->cch_end, h->nb_off, h->nb_idx, h->prange,
-                                                           h->spk_off, doff, nullptr, h->m2l_plan);
+                                                           h->spk_off, h->ccen, doff, nullptr, h->m2l_plan,
+                                                           h->m2l_plan_sh);
             NNCA_LAUNCH_CHECK();
         }
         std::vector<int4> v;
@@ -1178,6 +1239,78 @@ void build_finish(Handle *h) {
         if (!v.empty())
             NNCA_CUDA(cudaMemcpy(h->m2l_groups, v.data(), v.size() * sizeof(int4), cudaMemcpyHostToDevice));
         NNCA_CUDA(cudaStreamSynchronize(s));
+    }
+    {
+        // FP32 near field: packed point pairs, per-leaf plans and items
+        std::vector<int32_t> hpk(nc + 1, 0);
+        int64_t npairs = 0, maxpts = 0;
+        for (int64_t c = 0; c < nc; ++c) {
+            const int64_t pts = c >= leaf0 ? hce[c] - hcb[c] : 0;
+            maxpts = std::max(maxpts, pts);
+            npairs += m2l_padded((int)pts) / 2;
+            NNCA_REQUIRE(npairs < (1ll << 30), NNCA_ERR_UNSUPPORTED, "too many points for the FP32 near field");
+            hpk[c + 1] = (int32_t)npairs;
+        }
+        h->near_packed = maxpts <= 2 * NEAR_CAP;
+        if (h->near_packed) {
+            h->ppk_off = dalloc<int32_t>(h, nc + 1);
+            NNCA_CUDA(cudaMemcpy(h->ppk_off, hpk.data(), (nc + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+            h->ppk = dalloc<float4>(h, 4 * (size_t)npairs);
+            k_pack_near<<<grid_for(h->nleaf * 32, 256), 256, 0, s>>>(leaf0, leaf1, h->cbeg, h->cend, h->ppk_off, h->xh4,
+                                                                     h->xl4, h->ppk);
+            NNCA_LAUNCH_CHECK();
+            int64_t *dcnt = scr.get<int64_t>(h->nleaf), *doff = scr.get<int64_t>(h->nleaf);
+            k_near_plan<0><<<grid_for(h->nleaf, 128), 128, 0, s>>>(leaf0, leaf1, h->nb_off, h->nb_idx, h->ppk_off,
+                                                                   nullptr, dcnt, nullptr);
+            NNCA_LAUNCH_CHECK();
+            std::vector<int64_t> hcnt(h->nleaf), roff(h->nleaf + 1, 0);
+            NNCA_CUDA(cudaMemcpy(hcnt.data(), dcnt, h->nleaf * sizeof(int64_t), cudaMemcpyDeviceToHost));
+            for (int64_t i = 0; i < h->nleaf; ++i) roff[i + 1] = roff[i] + hcnt[i];
+            NNCA_REQUIRE(roff[h->nleaf] < (1ll << 31), NNCA_ERR_UNSUPPORTED, "near-field plan exceeds 2^31 records");
+            h->n_near_plan = roff[h->nleaf];
+            h->near_plan = dalloc<int4>(h, roff[h->nleaf]);
+            NNCA_CUDA(cudaMemcpy(doff, roff.data(), h->nleaf * sizeof(int64_t), cudaMemcpyHostToDevice));
+            k_near_plan<1><<<grid_for(h->nleaf, 128), 128, 0, s>>>(leaf0, leaf1, h->nb_off, h->nb_idx, h->ppk_off, doff,
+                                                                   nullptr, h->near_plan);
+            NNCA_LAUNCH_CHECK();
+            // items: one leaf each; its c targets sit TPL (2 or 3) per lane on
+            // L = ceil(c / TPL) lanes, and G = floor(32 / L) groups of L lanes
+            // split the source pairs. The TPL with the fewer idle target slots per
+            // unit of work (c G / (32 TPL) largest) wins. Heaviest first.
+            std::vector<std::pair<int64_t, int4>> its[2];
+            for (int64_t c = leaf0; c < leaf1; ++c) {
+                const int64_t nb = hce[c] - hcb[c];
+                if (nb == 0) continue;
+                int best = 0, bestG = 1;
+                double beste = -1.0;
+                for (int t = 2; t <= 3; ++t) {
+                    const int64_t L = (nb + t - 1) / t;
+                    if (L > 32) continue;
+                    const int G = (int)std::min<int64_t>(16, 32 / L);
+                    const double e = (double)nb * G / (32.0 * t);
+                    if (e > beste + 1e-12) {
+                        beste = e;
+                        best = t;
+                        bestG = G;
+                    }
+                }
+                NNCA_REQUIRE(best >= 2, NNCA_ERR_INTERNAL, "near-field layout: a leaf larger than 96 points");
+                its[best - 2].push_back({hp[c - leaf0],
+                                         make_int4((int)c, (int)(nb << 16) | (bestG << 24), (int)roff[c - leaf0],
+                                                   (int)(roff[c - leaf0 + 1] - roff[c - leaf0]))});
+            }
+            for (int t = 0; t < 2; ++t) {
+                std::stable_sort(its[t].begin(), its[t].end(),
+                                 [](const std::pair<int64_t, int4> &x, const std::pair<int64_t, int4> &y) { return x.first > y.first; });
+                std::vector<int4> v;
+                for (auto &p : its[t]) v.push_back(p.second);
+                h->n_near_items[t] = (int)v.size();
+                h->near_items[t] = dalloc<int4>(h, v.size());
+                if (!v.empty())
+                    NNCA_CUDA(cudaMemcpy(h->near_items[t], v.data(), v.size() * sizeof(int4), cudaMemcpyHostToDevice));
+            }
+            h->near_next = dalloc<int>(h, 2);
+        }
     }
     {
         std::vector<int32_t> cells;

@@ -115,14 +115,22 @@ unsigned grid_for(int64_t n, int threads, int64_t cap = 152 * 64) {
 }
 
 // ---- permutation into tree order --------------------------------------------
+// FP32 product (one right-hand side): also the float weight slot of each point
+// in the packed near-field pairs (leaf Y, local index j: pair ppk_off[Y] + j/2)
 template <class TI>
 __global__ void k_perm_in(const TI *x, int64_t ld, int64_t N, int64_t nrhs, const int32_t *perm, double *xt,
-                          float *xt32) {
+                          float *xt32, float *ppk_w, const int32_t *leaf_of, const int32_t *cbeg,
+                          const int32_t *ppk_off) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N * nrhs; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = e / N, i = e - r * N;
         const double v = (double)x[r * ld + perm[i]];
         xt[e] = v;
         if (xt32) xt32[e] = (float)v;
+        if (ppk_w) {
+            const int Y = leaf_of[i];
+            const int64_t j = i - cbeg[Y];
+            ppk_w[((int64_t)ppk_off[Y] + (j >> 1)) * 16 + 6 + (j & 1)] = (float)v;
+        }
     }
 }
 
@@ -533,7 +541,7 @@ __device__ __forceinline__ void unpack_item(int2 it, int &cell, int &a0, int &c)
 // block serves up to M2L_GROUP_TARGETS targets (pivots) of P's children, two
 // consecutive ones per lane, in their order (so a warp spans few children).
 // P's staging plan lists the children of N(P) with sources, each with the
-// mask of P's children that admit it, in rounds. Warp 0 stages a round with
+// mask of P's children that admit it, in rounds. One warp stages a round with
 // one bulk asynchronous copy (TMA) per cell from the packed sources into one of
 // M2L_STAGE_BUFS shared buffers, tracked by a "full" mbarrier, up to
 // M2L_STAGE_AHEAD rounds ahead of its own evaluation; the warps release each
@@ -585,6 +593,10 @@ __device__ __forceinline__ bool mbar_wait(void *bar, unsigned parity) {
         if (clock64() - t0 > (1ll << 31)) return false;
     }
 }
+// the same wait taken by a whole warp: it succeeds only if it succeeds for every lane
+__device__ __forceinline__ bool mbar_wait_warp(void *bar, unsigned parity) {
+    return __all_sync(0xffffffffu, mbar_wait(bar, parity));
+}
 // bulk copy global -> shared (16-byte aligned, size a multiple of 16), completing on bar
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, void *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -593,23 +605,39 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
                  : "memory");
 }
 
-// Warp 0: stage the round of plan records that starts at k into buffer b, for
-// its use-th use (after the warps have released its previous use). Returns the
-// first record of the next round, or kend after a timed-out wait.
-__device__ __forceinline__ int m2l_stage(M2lGroupSmem &S, int b, unsigned use, const int4 *plan, int k, int kend,
-                                         const float4 *spk, const float4 *chi, const float4 *clo, float4 hP,
-                                         float4 lP, unsigned *status) {
+// The staging warp's copy of the plan records of the next round: lane i holds
+// record k + i and its shift (loaded one round ahead, so staging never waits).
+struct StageCursor {
+    int k = 0;
+    int4 r = make_int4(0, 0, 0, 0);
+    float4 sh = make_float4(0.f, 0.f, 0.f, 0.f);
+};
+
+__device__ __forceinline__ void stage_load(StageCursor &c, const int4 *plan, const float4 *plan_sh, int k, int kend) {
     const int lane = threadIdx.x & 31;
-    if (use > 0 && !mbar_wait(&S.empty[b], (use - 1) & 1)) {
+    c.k = k;
+    if (k + lane < kend) {
+        c.r = plan[k + lane];
+        c.sh = plan_sh[k + lane];
+    }
+}
+
+// Staging warp: stage the round held by the cursor into buffer b, for its use-th use
+// (after the warps have released its previous use), then load the records of
+// the round after it. Returns the first record of that round, or kend after a
+// timed-out wait or a malformed record.
+__device__ __forceinline__ int m2l_stage(M2lGroupSmem &S, int b, unsigned use, StageCursor &cur, const int4 *plan,
+                                         const float4 *plan_sh, int kend, const float4 *spk, unsigned *status) {
+    const int lane = threadIdx.x & 31;
+    if (use > 0 && !mbar_wait_warp(&S.empty[b], (use - 1) & 1)) {
         if (lane == 0) {
             atomicOr(status, DEV_WAIT_TIMEOUT);
             *(volatile int *)&S.abort = 1;
         }
         return kend;
     }
-    int4 r = make_int4(0, 0, 0, 0);
-    if (k + lane < kend) r = plan[k + lane];
-    const int nrec = __shfl_sync(0xffffffffu, r.w, 0);   // cells in this round (first record)
+    const int k = cur.k;
+    const int nrec = __shfl_sync(0xffffffffu, cur.r.w, 0);   // cells in this round (first record)
     if (nrec < 1 || nrec > M2L_STAGE_RECS || k + nrec > kend) {   // a malformed plan: stop, never spin
         if (lane == 0) {
             atomicOr(status, DEV_BAD_INDEX);
@@ -618,11 +646,10 @@ __device__ __forceinline__ int m2l_stage(M2lGroupSmem &S, int b, unsigned use, c
         return kend;
     }
     unsigned bytes = 0;
+    const int4 r = cur.r;
     if (lane < nrec) {
         S.hdr[b][lane] = r.z;
-        const float4 hY = chi[r.x], lY = clo[r.x];
-        S.sh[b][lane] = make_float4((hY.x - hP.x) + (lY.x - lP.x), (hY.y - hP.y) + (lY.y - lP.y),
-                                    (hY.z - hP.z) + (lY.z - lP.z), 0.f);
+        S.sh[b][lane] = cur.sh;
         bytes = (unsigned)((r.z >> 11) & 0x7ff) * 32u;
     }
     const unsigned total = __reduce_add_sync(0xffffffffu, bytes);
@@ -631,6 +658,7 @@ __device__ __forceinline__ int m2l_stage(M2lGroupSmem &S, int b, unsigned use, c
     if (lane == 0) mbar_arrive_tx(&S.full[b], total);
     __syncwarp();
     if (lane < nrec) bulk_g2s(&S.src[b][r.z & 0x7ff][0], spk + 2 * (int64_t)r.y, bytes, &S.full[b]);
+    if (k + nrec < kend) stage_load(cur, plan, plan_sh, k + nrec, kend);
     return k + nrec;
 }
 
@@ -675,6 +703,7 @@ __device__ __forceinline__ f2 group_pair(const KParams &kp, const ulonglong2 &A,
 template <int KIND>
 __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group(KParams kp, const int4 *items, int nitems,
                                                                int *next_item, const int4 *plan,
+                                                               const float4 *plan_sh,
                                                                const int32_t *cch_beg, const int32_t *cch_end,
                                                                const int2 *prange, const float4 *pv4,
                                                                const float4 *chi, const float4 *clo,
@@ -689,7 +718,10 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group(KParams kp, con
         S.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    unsigned R = 0, Rp = 0;   // rounds consumed by every warp; rounds staged (warp 0)
+    // the staging warp: spread over the blocks so that every SM sub-partition
+    // (which holds the same warp index of each block) carries a share of it
+    const int pw = blockIdx.x % M2L_GROUP_WARPS;
+    unsigned R = 0, Rp = 0;   // rounds consumed by every warp; rounds staged (warp pw)
     for (;;) {
         __syncthreads();   // the previous item is done with the shared state
         if (tid == 0) S.item = atomicAdd(next_item, 1);
@@ -703,6 +735,8 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group(KParams kp, con
         __syncthreads();
         const float4 hP = chi[P], lP = clo[P];
         int kprod = item.z, kcons = item.z;
+        StageCursor cur;
+        if (wl == pw && kprod < kend) stage_load(cur, plan, plan_sh, kprod, kend);
         // this lane's two targets: pivots g and g + 1 of P's children
         const int j = t0 + wl * M2L_WARP_TARGETS + 2 * lane, jend = t0 + nt;
         const int g = S.ch_range[0].x + j;
@@ -712,15 +746,15 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group(KParams kp, con
         const unsigned omask =
             __reduce_or_sync(0xffffffffu, (Ta.c < 31 ? 1u << Ta.c : 0u) | (Tb.c < 31 ? 1u << Tb.c : 0u));
         while (kcons < kend) {
-            // warp 0 keeps up to M2L_STAGE_AHEAD rounds staged beyond the one it evaluates
-            if (wl == 0)
+            // warp pw keeps up to M2L_STAGE_AHEAD rounds staged beyond the one it evaluates
+            if (wl == pw)
                 while (kprod < kend && Rp <= R + M2L_STAGE_AHEAD) {
-                    kprod = m2l_stage(S, Rp % M2L_STAGE_BUFS, Rp / M2L_STAGE_BUFS, plan, kprod, kend, spk, chi, clo,
-                                      hP, lP, status);
+                    kprod = m2l_stage(S, Rp % M2L_STAGE_BUFS, Rp / M2L_STAGE_BUFS, cur, plan, plan_sh, kend, spk,
+                                      status);
                     ++Rp;
                 }
             const int b = R % M2L_STAGE_BUFS;
-            if (!mbar_wait(&S.full[b], (R / M2L_STAGE_BUFS) & 1)) {
+            if (!mbar_wait_warp(&S.full[b], (R / M2L_STAGE_BUFS) & 1)) {
                 if (lane == 0) {
                     atomicOr(status, DEV_WAIT_TIMEOUT);
                     *(volatile int *)&S.abort = 1;
@@ -764,7 +798,7 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group(KParams kp, con
         if (Tb.c < 31) u[Tb.g] = kp.s * ((double)Tb.sum + (double)Tb.comp);
     }
     // after a timed-out wait: let copies still in flight land before the block exits
-    if (tid == 0)
+    if (wl == pw && lane == 0)
         for (unsigned r = R; r < Rp; ++r) mbar_wait(&S.full[r % M2L_STAGE_BUFS], (r / M2L_STAGE_BUFS) & 1);
 }
 
@@ -873,6 +907,217 @@ __global__ void __launch_bounds__(32 * MV_WARPS) k_leaf_f32(KParams kp, const in
             y[perm[i]] = (TO)yv;
         }
     }
+}
+
+// ---- leaves: L2P (FP64) + P2P (FP32, hi/lo coordinates), one warp per leaf -------
+// A warp serves the c targets of one leaf: TPL consecutive targets per lane on
+// L = ceil(c / TPL) lanes, and G = floor(32 / L) groups of L lanes that split
+// the source pairs of every cell (the layout is chosen per leaf at build time
+// to leave few target slots idle). The points of N(B) arrive by bulk
+// asynchronous copies (TMA), one per cell, from the packed point pairs into
+// NEAR_BUFS buffers of the warp, each tracked by its own mbarrier; the warp
+// stages up to two rounds ahead of its evaluation, so no other warp takes part.
+// Each cell is summed in float and added into a compensated total; pairs of B
+// with itself are guarded against r = 0 (the diagonal takes the configured
+// value afterwards).
+struct NearWarpSmem {
+    float4 src[NEAR_BUFS][NEAR_CAP][4];   // point pairs: hi xy, hi z + weights, lo xy, lo z
+    int hdr[NEAR_BUFS][NEAR_RECS];        // slot | pairs << 11 | own leaf << 22
+    int nrec[NEAR_BUFS];
+    unsigned long long full[NEAR_BUFS];   // mbarriers
+};
+
+struct NearTarget {
+    bool act = false;
+    int i = 0;   // sorted position
+    f2 xh = 0ull, yh = 0ull, zh = 0ull, xl = 0ull, yl = 0ull, zl = 0ull;   // (t, t) packed
+    float sum = 0.f, comp = 0.f;
+};
+
+__device__ __forceinline__ void near_target(NearTarget &T, bool act, int i, const float4 *xh4, const float4 *xl4) {
+    T.act = act;
+    T.i = i;
+    if (!act) return;
+    const float4 h = xh4[i], l = xl4[i];
+    T.xh = f2_pack(h.x, h.x);
+    T.yh = f2_pack(h.y, h.y);
+    T.zh = f2_pack(h.z, h.z);
+    T.xl = f2_pack(l.x, l.x);
+    T.yl = f2_pack(l.y, l.y);
+    T.zl = f2_pack(l.z, l.z);
+}
+
+// acc += f(|s - t|^2) w over a packed pair of sources; (hi_s - hi_t) + (lo_s - lo_t) per coordinate
+template <int KIND, bool SAFE>
+__device__ __forceinline__ f2 near_pair(const KParams &kp, const ulonglong2 &A, const ulonglong2 &B,
+                                        const ulonglong2 &C, const ulonglong2 &D, const NearTarget &T, f2 acc) {
+    const f2 dx = f2_add(f2_sub(A.x, T.xh), f2_sub(C.x, T.xl));
+    const f2 dy = f2_add(f2_sub(A.y, T.yh), f2_sub(C.y, T.yl));
+    const f2 dz = f2_add(f2_sub(B.x, T.zh), f2_sub(D.x, T.zl));
+    f2 r2 = f2_mul(dx, dx);
+    r2 = f2_fma(dy, dy, r2);
+    r2 = f2_fma(dz, dz, r2);
+    return f2_fma(KF2<KIND, SAFE>::eval(kp, r2), B.y, acc);
+}
+
+// Stage the round of plan records held by the warp (lane i: record k + i) into buffer b.
+__device__ __forceinline__ int near_stage(NearWarpSmem &W, int b, const int4 &r, int k, int kend, const float4 *ppk,
+                                          unsigned *status) {
+    const int lane = threadIdx.x & 31;
+    const int nrec = __shfl_sync(0xffffffffu, r.w, 0);
+    if (nrec < 1 || nrec > NEAR_RECS || k + nrec > kend) {   // a malformed plan: stop, never spin
+        if (lane == 0) atomicOr(status, DEV_BAD_INDEX);
+        return -1;
+    }
+    unsigned bytes = 0;
+    if (lane < nrec) {
+        W.hdr[b][lane] = r.z;
+        bytes = (unsigned)((r.z >> 11) & 0x7ff) * 64u;
+    }
+    const unsigned total = __reduce_add_sync(0xffffffffu, bytes);
+    if (lane == 0) W.nrec[b] = nrec;
+    // the buffer's previous contents were read by this warp's generic loads
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) mbar_arrive_tx(&W.full[b], total);
+    __syncwarp();
+    if (lane < nrec) bulk_g2s(&W.src[b][r.z & 0x7ff][0], ppk + 4 * (int64_t)r.y, bytes, &W.full[b]);
+    return k + nrec;
+}
+
+// one cell: this lane's group takes source pairs q0 + g, q0 + g + G, ...
+template <int KIND, int TPL, bool SAFE>
+__device__ __forceinline__ void near_cell(const KParams &kp, const NearWarpSmem &W, int b, int q0, int q1, int g,
+                                          int G, NearTarget (&T)[TPL]) {
+    f2 acc[TPL][2];
+#pragma unroll
+    for (int k = 0; k < TPL; ++k) acc[k][0] = acc[k][1] = 0ull;
+    for (int q = q0 + g; q < q1; q += 2 * G) {
+        {
+            const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(&W.src[b][q][0]);
+            const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(&W.src[b][q][1]);
+            const ulonglong2 C = *reinterpret_cast<const ulonglong2 *>(&W.src[b][q][2]);
+            const ulonglong2 D = *reinterpret_cast<const ulonglong2 *>(&W.src[b][q][3]);
+#pragma unroll
+            for (int k = 0; k < TPL; ++k) acc[k][0] = near_pair<KIND, SAFE>(kp, A, B, C, D, T[k], acc[k][0]);
+        }
+        if (q + G < q1) {
+            const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(&W.src[b][q + G][0]);
+            const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(&W.src[b][q + G][1]);
+            const ulonglong2 C = *reinterpret_cast<const ulonglong2 *>(&W.src[b][q + G][2]);
+            const ulonglong2 D = *reinterpret_cast<const ulonglong2 *>(&W.src[b][q + G][3]);
+#pragma unroll
+            for (int k = 0; k < TPL; ++k) acc[k][1] = near_pair<KIND, SAFE>(kp, A, B, C, D, T[k], acc[k][1]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < TPL; ++k) {
+        const float2 p = f2_unpack(f2_add(acc[k][0], acc[k][1]));
+        two_sum_add(T[k].sum, T[k].comp, p.x + p.y);
+    }
+}
+
+template <int KIND, int TPL, class TO>
+__global__ void __launch_bounds__(32 * NEAR_WARPS) k_near_group(KParams kp, const int4 *items, int nitems,
+                                                               int *next_item, const int4 *plan, const int32_t *cbeg,
+                                                               const int32_t *piv_off, const int64_t *op_off,
+                                                               const double *op, const double *u, const float4 *xh4,
+                                                               const float4 *xl4, const float4 *ppk,
+                                                               const double *xt64, const int32_t *perm, TO *y,
+                                                               unsigned *status) {
+    __shared__ __align__(128) NearWarpSmem Sm[NEAR_WARPS];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    NearWarpSmem &W = Sm[wl];
+    if (lane == 0) {
+        for (int b = 0; b < NEAR_BUFS; ++b) mbar_init(&W.full[b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const float k0 = KF<KIND>::f32(kp, 0.f);
+    unsigned R = 0, Rp = 0;   // rounds consumed, rounds staged
+    bool failed = false;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(next_item, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= nitems || failed) break;
+        const int4 item = items[it];
+        const int B = item.x, c = (item.y >> 16) & 0xff, G = (item.y >> 24) & 0x1f, kend = item.z + item.w;
+        const int L = (c + TPL - 1) / TPL;
+        const int g = lane / L, ti = lane - g * L;   // group, lane within the group
+        const bool live = g < G;
+        const int i0 = cbeg[B];
+        NearTarget T[TPL];
+#pragma unroll
+        for (int k = 0; k < TPL; ++k) near_target(T[k], live && ti * TPL + k < c, i0 + ti * TPL + k, xh4, xl4);
+        int kprod = item.z, kcons = item.z;
+        int4 rec = make_int4(0, 0, 0, 0);
+        if (kprod + lane < kend) rec = plan[kprod + lane];
+        while (kcons < kend) {
+            // stage up to two rounds beyond the one evaluated (the third buffer is free)
+            while (kprod < kend && Rp <= R + NEAR_BUFS - 2) {
+                const int kn = near_stage(W, Rp % NEAR_BUFS, rec, kprod, kend, ppk, status);
+                if (kn < 0) {
+                    kprod = kend;
+                    failed = true;
+                    break;
+                }
+                kprod = kn;
+                ++Rp;
+                if (kprod + lane < kend) rec = plan[kprod + lane];
+            }
+            if (failed) break;
+            const int b = R % NEAR_BUFS;
+            if (!mbar_wait_warp(&W.full[b], (R / NEAR_BUFS) & 1)) {
+                if (lane == 0) atomicOr(status, DEV_WAIT_TIMEOUT);
+                failed = true;
+                break;
+            }
+            const int nrec = W.nrec[b];
+            if (live)
+                for (int e = 0; e < nrec; ++e) {
+                    const int hw = W.hdr[b][e];
+                    const int q0 = hw & 0x7ff, q1 = q0 + ((hw >> 11) & 0x7ff);
+                    if ((hw >> 22) & 1) near_cell<KIND, TPL, true>(kp, W, b, q0, q1, g, G, T);
+                    else near_cell<KIND, TPL, false>(kp, W, b, q0, q1, g, G, T);
+                }
+            __syncwarp();
+            ++R;
+            kcons += nrec;
+        }
+        if (failed) break;
+        // the groups summed disjoint source pairs of the same targets: combine into group 0
+        for (int gg = 1; gg < G; ++gg) {
+            const int srcl = min(ti + gg * L, 31);
+#pragma unroll
+            for (int k = 0; k < TPL; ++k) {
+                const float so = __shfl_sync(0xffffffffu, T[k].sum, srcl);
+                const float co = __shfl_sync(0xffffffffu, T[k].comp, srcl);
+                if (g == 0) {
+                    two_sum_add(T[k].sum, T[k].comp, so);
+                    T[k].comp += co;
+                }
+            }
+        }
+        if (g == 0) {
+            // L2P in FP64, then the diagonal: the pair (i, i) was evaluated as K(0)
+            const int r = piv_off[B + 1] - piv_off[B];
+            const double *uB = u + piv_off[B];
+#pragma unroll
+            for (int k = 0; k < TPL; ++k) {
+                if (!T[k].act) continue;
+                const double *Urow = op + op_off[B] + (int64_t)(T[k].i - i0) * r;
+                double far = 0.0;
+                for (int bb = 0; bb < r; ++bb) far = fma(Urow[bb], uB[bb], far);
+                const double near = (double)T[k].sum + (double)T[k].comp;
+                const double yv = far + kp.s * near + (kp.diag - kp.s * (double)k0) * xt64[T[k].i];
+                y[perm[T[k].i]] = (TO)yv;
+            }
+        }
+    }
+    // after a failure: let copies still in flight land before the warp exits
+    if (lane == 0)
+        for (unsigned r = R; r < Rp; ++r) mbar_wait(&W.full[r % NEAR_BUFS], (r / NEAR_BUFS) & 1);
 }
 
 // ---- leaves: L2P + P2P, FP64 -------------------------------------------------
@@ -1024,7 +1269,7 @@ void launch_m2l_f32(Handle *h, double *u) {
     const unsigned g = (unsigned)std::min<int64_t>(h->n_m2l_groups, (int64_t)nsm * std::max(1, per_sm));
     NNCA_CUDA(cudaMemsetAsync(h->m2l_next, 0, sizeof(int), h->stream));
     k_m2l_group<KIND><<<g, M2L_GROUP_THREADS, 0, h->stream>>>(h->kp, h->m2l_groups, h->n_m2l_groups, h->m2l_next,
-                                                             h->m2l_plan, h->cch_beg, h->cch_end, h->prange, h->pv4,
+                                                             h->m2l_plan, h->m2l_plan_sh, h->cch_beg, h->cch_end, h->prange, h->pv4,
                                                              h->chi4, h->clo4, h->spk, u, h->dev_status);
     NNCA_LAUNCH_CHECK();
     ++h->launches;
@@ -1032,6 +1277,32 @@ void launch_m2l_f32(Handle *h, double *u) {
 
 template <int KIND, class TO>
 void launch_leaf_f32(Handle *h, const double *op, const double *u, const float *xt32, const double *xt64, TO *y) {
+    if (h->near_packed) {
+        int dev = 0, nsm = 152;
+        NNCA_CUDA(cudaGetDevice(&dev));
+        NNCA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        NNCA_CUDA(cudaMemsetAsync(h->near_next, 0, 2 * sizeof(int), h->stream));
+        for (int t = 0; t < 2; ++t) {
+            const int n = h->n_near_items[t];
+            if (!n) continue;
+            int per_sm = 1;
+#define NNCA_NEAR(TPL)                                                                                                 \
+    do {                                                                                                               \
+        NNCA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_near_group<KIND, TPL, TO>, 32 * NEAR_WARPS, 0)); \
+        const int64_t warps = (int64_t)nsm * std::max(1, per_sm) * NEAR_WARPS;                                         \
+        const unsigned g = (unsigned)((std::min<int64_t>(n, warps) + NEAR_WARPS - 1) / NEAR_WARPS);                    \
+        k_near_group<KIND, TPL, TO><<<g, 32 * NEAR_WARPS, 0, h->stream>>>(                                             \
+            h->kp, h->near_items[t], n, h->near_next + t, h->near_plan, h->cbeg, h->piv_off, h->op_off, op, u, h->xh4, \
+            h->xl4, h->ppk, xt64, h->perm, y, h->dev_status);                                                          \
+    } while (0)
+            if (t == 0) NNCA_NEAR(2);
+            else NNCA_NEAR(3);
+#undef NNCA_NEAR
+            NNCA_LAUNCH_CHECK();
+            ++h->launches;
+        }
+        return;
+    }
     for (int ls = 0; ls < 5; ++ls) {
         const int n = h->n_leaf_items[ls];
         if (!n) continue;
@@ -1080,7 +1351,9 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
     const TO *xin = (const TO *)x + r0 * ld;
     TO *yout = (TO *)y + r0 * ld;
     prof_mark(h, 0);
-    k_perm_in<TO><<<grid_for(N * NR, 256), 256, 0, s>>>(xin, ld, N, NR, h->perm, xt, xt32);
+    float *ppk_w = FP32 && kernel_is_radial(h->kp.kind) && h->near_packed ? reinterpret_cast<float *>(h->ppk) : nullptr;
+    k_perm_in<TO><<<grid_for(N * NR, 256), 256, 0, s>>>(xin, ld, N, NR, h->perm, xt, xt32, ppk_w, h->leaf_of, h->cbeg,
+                                                        h->ppk_off);
     NNCA_LAUNCH_CHECK();
     ++h->launches;
     prof_mark(h, 1);

@@ -171,6 +171,14 @@ constexpr int M2L_GROUP_TARGETS = M2L_WARP_TARGETS * M2L_GROUP_WARPS;
 constexpr int M2L_STAGE_CAP = 512;
 constexpr int M2L_STAGE_RECS = 32;
 constexpr int M2L_STAGE_BUFS = 4;
+// The FP32 near field runs independent warps, NEAR_WARPS per block, one leaf
+// (up to 64 targets) per work item. The points of N(B) arrive in rounds of at
+// most NEAR_RECS cells and NEAR_CAP point pairs through NEAR_BUFS buffers per
+// warp, which bounds the largest leaf it takes (2 * NEAR_CAP points).
+constexpr int NEAR_WARPS = 4;
+constexpr int NEAR_CAP = 48;
+constexpr int NEAR_RECS = 32;
+constexpr int NEAR_BUFS = 3;
 // coordinate of a padding source: far from every target, weight 0
 constexpr float FAR_AWAY = 1.0e18f;
 // sources of a cell padded to a multiple of four (two packed pairs)
@@ -260,8 +268,24 @@ struct Handle {
     int4 *m2l_groups = nullptr;
     int n_m2l_groups = 0;
     int *m2l_next = nullptr;      // item counter of the FP32 M2L launch
+    // FP32 near field: points of every leaf as pairs [xh0 xh1 yh0 yh1][zh0 zh1 w0 w1]
+    // [xl0 xl1 yl0 yl1][zl0 zl1 0 0] (absolute coordinates as float hi + lo,
+    // padded to m2l_padded(points) with far-away points of weight 0; the
+    // products write the weights) from pair ppk_off[cell]; per-leaf staging plans
+    // (cell, first pair, slot | pairs << 11 | own leaf << 22, cells in the round
+    // or 0) and items (leaf, first target | targets << 16 | groups << 24, first
+    // record, records) for 2 and 3 targets per lane
+    float4 *ppk = nullptr;
+    int32_t *ppk_off = nullptr;   // [ncell + 1]
+    int4 *near_plan = nullptr;
+    int64_t n_near_plan = 0;
+    int4 *near_items[2] = {nullptr, nullptr};   // by targets per lane (2, 3)
+    int n_near_items[2] = {0, 0};
+    int *near_next = nullptr;                    // [2] item counters
+    bool near_packed = false;     // false: leaves too large, the ring kernel serves them
     const char *m2l_fp32_unsupported = nullptr;   // why the FP32 M2L cannot run, or null
     int4 *m2l_plan = nullptr;
+    float4 *m2l_plan_sh = nullptr;   // per plan record: c_Y - c_P rounded to float
     int64_t n_m2l_plan = 0;
     float4 *spk = nullptr;
     int32_t *spk_off = nullptr;   // [ncell + 1]
