@@ -317,7 +317,7 @@ def run_ours(args):
     peak_gpair = MUFU_PER_CLK_SM * SMS * sm_max * 1e6 / 1e9
     achieved = st["m2l_pairs"] / (m2l_ms / 1e3) / 1e9
     traffic = None
-    tf = os.path.join(ROOT, "profiles", "m2l_f32_traffic_invr3d.json")
+    tf = os.path.join(ROOT, "profiles", "m2l_group_traffic_invr3d.json")
     if os.path.exists(tf):
         try:
             traffic = json.load(open(tf)).get("bytes_per_launch")
@@ -344,10 +344,10 @@ def run_ours(args):
         "work": {"m2l_pairs": st["m2l_pairs"], "p2p_pairs": st["p2p_pairs"]},
         "pass_ms": {"perm": pass_ms[0], "p2m_m2m": pass_ms[1], "m2l": pass_ms[2], "l2l": pass_ms[3],
                     "l2p_p2p": pass_ms[4], "total": pass_ms[5]},
-        "roofline": {"bound": "alu", "kernel": "k_m2l_f32", "achieved": achieved, "peak": peak_gpair,
+        "roofline": {"bound": "alu", "kernel": "k_m2l_group", "achieved": achieved, "peak": peak_gpair,
                      "unit": "Gpair/s", "frac": achieved / peak_gpair, "traffic": traffic,
                      "peak_note": f"MUFU rsqrt issue rate {MUFU_PER_CLK_SM}/clk/SM x {SMS} SMs x {sm_max:.0f} MHz",
-                     "traffic_note": "DRAM bytes of one M2L pass (its 5 launches), ncu at N=131072 scaled by N"},
+                     "traffic_note": "DRAM bytes of one M2L launch, ncu at N=131072 scaled by N"},
         "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": N * nrhs * 8,
                 "d2h_bytes_per_step": N * nrhs * 8, "matches_device_result": e2e_ok},
         "gpu_launches": int(st_prof["launches_per_product"]) * args.steps,
