@@ -700,6 +700,25 @@ __device__ __forceinline__ f2 group_pair(const KParams &kp, const ulonglong2 &A,
     return f2_fma(KF2<KIND, false>::eval(kp, r2), B.y, acc);
 }
 
+// the source pairs q0, q0 + step, ... below q1 (pairs taken two at a time) of one
+// staged cell against two targets; FULL: the whole warp, step 2
+template <int KIND, int FULL>
+__device__ __forceinline__ void m2l_cell_pairs(const KParams &kp, const float4 (*src)[2], int q0, int q1, f2 xa, f2 ya,
+                                               f2 za, f2 xb, f2 yb, f2 zb, f2 &a0, f2 &a1, f2 &b0, f2 &b1,
+                                               int step = 2) {
+    if (FULL) step = 2;
+    for (int q = q0; q < q1; q += step) {
+        const ulonglong2 A0 = *reinterpret_cast<const ulonglong2 *>(&src[q][0]);
+        const ulonglong2 B0 = *reinterpret_cast<const ulonglong2 *>(&src[q][1]);
+        const ulonglong2 A1 = *reinterpret_cast<const ulonglong2 *>(&src[q + 1][0]);
+        const ulonglong2 B1 = *reinterpret_cast<const ulonglong2 *>(&src[q + 1][1]);
+        a0 = group_pair<KIND>(kp, A0, B0, xa, ya, za, a0);
+        b0 = group_pair<KIND>(kp, A0, B0, xb, yb, zb, b0);
+        a1 = group_pair<KIND>(kp, A1, B1, xa, ya, za, a1);
+        b1 = group_pair<KIND>(kp, A1, B1, xb, yb, zb, b1);
+    }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group(KParams kp, const int4 *items, int nitems,
                                                                int *next_item, const int4 *plan,
@@ -737,12 +756,19 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group(KParams kp, con
         int kprod = item.z, kcons = item.z;
         StageCursor cur;
         if (wl == pw && kprod < kend) stage_load(cur, plan, plan_sh, kprod, kend);
-        // this lane's two targets: pivots g and g + 1 of P's children
-        const int j = t0 + wl * M2L_WARP_TARGETS + 2 * lane, jend = t0 + nt;
+        // this warp's cw targets sit two per lane on L lanes; in a partial warp
+        // G groups of L lanes split the source pairs of every cell
+        const int wj0 = t0 + wl * M2L_WARP_TARGETS, jend = t0 + nt;
+        const int cw = min(M2L_WARP_TARGETS, max(0, jend - wj0));
+        const int L = cw > 0 ? (cw + 1) / 2 : 32;
+        const int G = min(16, 32 / L);
+        const int grp = lane / L, ti = lane - grp * L;
+        const bool live = grp < G;
+        const int j = wj0 + 2 * ti;
         const int g = S.ch_range[0].x + j;
         GroupTarget Ta, Tb;
-        group_target(Ta, j < jend, g, nch, cb, S.ch_range, pv4, chi, clo, hP, lP);
-        group_target(Tb, j + 1 < jend, g + 1, nch, cb, S.ch_range, pv4, chi, clo, hP, lP);
+        group_target(Ta, live && j < jend, g, nch, cb, S.ch_range, pv4, chi, clo, hP, lP);
+        group_target(Tb, live && j + 1 < jend, g + 1, nch, cb, S.ch_range, pv4, chi, clo, hP, lP);
         const unsigned omask =
             __reduce_or_sync(0xffffffffu, (Ta.c < 31 ? 1u << Ta.c : 0u) | (Tb.c < 31 ? 1u << Tb.c : 0u));
         while (kcons < kend) {
@@ -763,7 +789,7 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group(KParams kp, con
             }
             const int nrec = S.nrec[b];
             if (nrec < 1) break;   // unreachable with a well-formed plan
-            if (omask) {
+            if (omask && live) {
                 for (int i = 0; i < nrec; ++i) {
                     const int hw = S.hdr[b][i];
                     const unsigned m = ((unsigned)hw >> 22) & omask;
@@ -774,16 +800,11 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group(KParams kp, con
                     const f2 xb = f2_sub(Tb.tx, SX), yb = f2_sub(Tb.ty, SY), zb = f2_sub(Tb.tz, SZ);
                     const int q0 = hw & 0x7ff, q1 = q0 + ((hw >> 11) & 0x7ff);
                     f2 a0 = 0ull, a1 = 0ull, b0 = 0ull, b1 = 0ull;
-                    for (int q = q0; q < q1; q += 2) {
-                        const ulonglong2 A0 = *reinterpret_cast<const ulonglong2 *>(&S.src[b][q][0]);
-                        const ulonglong2 B0 = *reinterpret_cast<const ulonglong2 *>(&S.src[b][q][1]);
-                        const ulonglong2 A1 = *reinterpret_cast<const ulonglong2 *>(&S.src[b][q + 1][0]);
-                        const ulonglong2 B1 = *reinterpret_cast<const ulonglong2 *>(&S.src[b][q + 1][1]);
-                        a0 = group_pair<KIND>(kp, A0, B0, xa, ya, za, a0);
-                        b0 = group_pair<KIND>(kp, A0, B0, xb, yb, zb, b0);
-                        a1 = group_pair<KIND>(kp, A1, B1, xa, ya, za, a1);
-                        b1 = group_pair<KIND>(kp, A1, B1, xb, yb, zb, b1);
-                    }
+                    if (G == 1)
+                        m2l_cell_pairs<KIND, 1>(kp, S.src[b], q0, q1, xa, ya, za, xb, yb, zb, a0, a1, b0, b1);
+                    else
+                        m2l_cell_pairs<KIND, 0>(kp, S.src[b], q0 + 2 * grp, q1, xa, ya, za, xb, yb, zb, a0, a1, b0, b1,
+                                                2 * G);
                     const float2 pa = f2_unpack(f2_add(a0, a1)), pb = f2_unpack(f2_add(b0, b1));
                     if ((m >> Ta.c) & 1u) two_sum_add(Ta.sum, Ta.comp, pa.x + pa.y);
                     if ((m >> Tb.c) & 1u) two_sum_add(Tb.sum, Tb.comp, pb.x + pb.y);
@@ -794,8 +815,20 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group(KParams kp, con
             ++R;
             kcons += nrec;
         }
-        if (Ta.c < 31) u[Ta.g] = kp.s * ((double)Ta.sum + (double)Ta.comp);
-        if (Tb.c < 31) u[Tb.g] = kp.s * ((double)Tb.sum + (double)Tb.comp);
+        // the groups summed disjoint source pairs of the same targets: combine into group 0
+        for (int gg = 1; gg < G; ++gg) {
+            const int srcl = min(ti + gg * L, 31);
+            const float sa = __shfl_sync(0xffffffffu, Ta.sum, srcl), ca = __shfl_sync(0xffffffffu, Ta.comp, srcl);
+            const float sb = __shfl_sync(0xffffffffu, Tb.sum, srcl), cb2 = __shfl_sync(0xffffffffu, Tb.comp, srcl);
+            if (grp == 0) {
+                two_sum_add(Ta.sum, Ta.comp, sa);
+                Ta.comp += ca;
+                two_sum_add(Tb.sum, Tb.comp, sb);
+                Tb.comp += cb2;
+            }
+        }
+        if (grp == 0 && Ta.c < 31) u[Ta.g] = kp.s * ((double)Ta.sum + (double)Ta.comp);
+        if (grp == 0 && Tb.c < 31) u[Tb.g] = kp.s * ((double)Tb.sum + (double)Tb.comp);
     }
     // after a timed-out wait: let copies still in flight land before the block exits
     if (wl == pw && lane == 0)
