@@ -176,6 +176,20 @@ nnca_status nnca_matvec_host(nnca_handle h, const void *x_host, void *y_host, in
 nnca_status nnca_matvec_noalloc(nnca_handle h, const void *x, void *y, int64_t ld, int dtype, int precision,
                                 void *stream);
 
+/* Products of `count` independent handles at once (batched uneven problems; the
+ * paper has no counterpart). Product k is y[k] = A_k x[k] for handle h[k] with
+ * leading dimension ld[k] (>= that handle's n); nrhs, dtype and precision are
+ * shared. The products run on internal worker streams forked from `stream` and
+ * joined back to it (event waits), so small problems overlap on the GPU and the
+ * call as a whole is ordered on `stream`. Capturing `stream` into a CUDA graph
+ * captures all of it: make one uncaptured call first with the same handles and
+ * nrhs (it allocates the handles' workspaces and the worker streams). A handle
+ * may appear at most once per call. Errors: NNCA_ERR_INVALID_ARG for NULL
+ * arrays, count < 1 or > 4096, a repeated handle, or any argument nnca_matvec
+ * would reject (nnca_last_error(NULL) names the first failing product). */
+nnca_status nnca_matvec_batch(const nnca_handle *h, int count, const void *const *x, void *const *y,
+                              const int64_t *ld, int64_t nrhs, int dtype, int precision, void *stream);
+
 /* Free every device and host resource of the handle (NULL is a no-op).
  * Synchronises the device first. */
 void nnca_destroy(nnca_handle h);

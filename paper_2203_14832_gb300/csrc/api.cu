@@ -5,6 +5,8 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <set>
 
 #include "nnca_internal.cuh"
 
@@ -247,6 +249,80 @@ nnca_status nnca_matvec(nnca_handle h, const void *x, void *y, int64_t nrhs, int
         return fail(h, e.status, e.what());
     } catch (const std::exception &e) {
         return fail(h, NNCA_ERR_INTERNAL, e.what());
+    }
+    return NNCA_OK;
+}
+
+namespace {
+
+// Worker streams of nnca_matvec_batch, per device, created once and kept.
+constexpr int kBatchStreams = 16;
+struct BatchPool {
+    cudaStream_t s[kBatchStreams] = {};
+    cudaEvent_t fork = nullptr, join[kBatchStreams] = {};
+    bool ready = false;
+};
+std::mutex g_batch_mutex;
+BatchPool g_batch_pool[64];
+
+BatchPool &batch_pool() {
+    int dev = 0;
+    NNCA_CUDA(cudaGetDevice(&dev));
+    NNCA_REQUIRE(dev >= 0 && dev < 64, NNCA_ERR_UNSUPPORTED, "nnca_matvec_batch: device index above 63");
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    BatchPool &P = g_batch_pool[dev];
+    if (!P.ready) {
+        for (int i = 0; i < kBatchStreams; ++i) {
+            NNCA_CUDA(cudaStreamCreateWithFlags(&P.s[i], cudaStreamNonBlocking));
+            NNCA_CUDA(cudaEventCreateWithFlags(&P.join[i], cudaEventDisableTiming));
+        }
+        NNCA_CUDA(cudaEventCreateWithFlags(&P.fork, cudaEventDisableTiming));
+        P.ready = true;
+    }
+    return P;
+}
+
+}  // namespace
+
+nnca_status nnca_matvec_batch(const nnca_handle *hs, int count, const void *const *x, void *const *y,
+                              const int64_t *ld, int64_t nrhs, int dtype, int precision, void *stream) {
+    if (!hs || !x || !y || !ld) return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_matvec_batch: NULL array");
+    if (count < 1 || count > 4096) return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_matvec_batch: count must be 1..4096");
+    if (nrhs < 1) return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_matvec_batch: nrhs must be >= 1");
+    if (dtype != NNCA_F64 && dtype != NNCA_F32) return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_matvec_batch: unknown dtype");
+    if (precision != NNCA_PREC_FP64 && precision != NNCA_PREC_FP32)
+        return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_matvec_batch: unknown precision");
+    std::set<const void *> seen;
+    for (int k = 0; k < count; ++k) {
+        const std::string at = "nnca_matvec_batch: product " + std::to_string(k) + ": ";
+        if (!hs[k]) return fail(nullptr, NNCA_ERR_INVALID_ARG, at + "NULL handle");
+        if (!seen.insert(hs[k]).second) return fail(nullptr, NNCA_ERR_INVALID_ARG, at + "handle repeated");
+        if (!x[k] || !y[k]) return fail(nullptr, NNCA_ERR_INVALID_ARG, at + "NULL x or y");
+        if (ld[k] < hs[k]->n) return fail(nullptr, NNCA_ERR_INVALID_ARG, at + "ld below n");
+        if (!is_device_ptr(x[k]) || !is_device_ptr(y[k]))
+            return fail(nullptr, NNCA_ERR_INVALID_ARG, at + "x and y must be device memory");
+    }
+    int k = 0;
+    try {
+        BatchPool &P = batch_pool();
+        const cudaStream_t s = (cudaStream_t)stream;
+        const int nw = std::min(count, kBatchStreams);
+        NNCA_CUDA(cudaEventRecord(P.fork, s));
+        for (int i = 0; i < nw; ++i) NNCA_CUDA(cudaStreamWaitEvent(P.s[i], P.fork, 0));
+        for (k = 0; k < count; ++k) {
+            Handle *h = hs[k];
+            h->stream = P.s[k % nw];
+            matvec(h, x[k], y[k], nrhs, ld[k], dtype, precision);
+            h->stats.launches_per_product = h->launches;
+        }
+        for (int i = 0; i < nw; ++i) {
+            NNCA_CUDA(cudaEventRecord(P.join[i], P.s[i]));
+            NNCA_CUDA(cudaStreamWaitEvent(s, P.join[i], 0));
+        }
+    } catch (const Error &e) {
+        return fail(k < count ? hs[k] : nullptr, e.status, "nnca_matvec_batch: product " + std::to_string(k) + ": " + e.what());
+    } catch (const std::exception &e) {
+        return fail(nullptr, NNCA_ERR_INTERNAL, e.what());
     }
     return NNCA_OK;
 }

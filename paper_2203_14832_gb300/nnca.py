@@ -79,6 +79,9 @@ def lib() -> C.CDLL:
         L.nnca_export.argtypes = [vp, C.c_int, vp, C.c_int64, C.POINTER(C.c_int64)]
         L.nnca_matvec_noalloc.restype = C.c_int
         L.nnca_matvec_noalloc.argtypes = [vp, vp, vp, C.c_int64, C.c_int, C.c_int, vp]
+        L.nnca_matvec_batch.restype = C.c_int
+        L.nnca_matvec_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(C.c_int64),
+                                        C.c_int64, C.c_int, C.c_int, vp]
         L.nnca_set_profiling.restype = C.c_int
         L.nnca_set_profiling.argtypes = [vp, C.c_int]
         L.nnca_last_error.restype = C.c_char_p
@@ -143,6 +146,21 @@ def nnca_matvec(handle, x, y, nrhs: int, ld: int, precision: int = PREC_FP64, st
     assert x.dtype == y.dtype and x.is_cuda and y.is_cuda
     _check(lib().nnca_matvec(handle, x.data_ptr(), y.data_ptr(), nrhs, ld, dtype, precision, _stream_ptr(stream)),
            handle)
+
+
+def nnca_matvec_batch(handles, xs, ys, nrhs: int, lds, precision: int = PREC_FP64, stream=None):
+    """y_k = A_k x_k for independent handles at once (CUDA tensors of one dtype)."""
+    import torch
+    k = len(handles)
+    assert k == len(xs) == len(ys) == len(lds) and k > 0
+    dtype = F64 if xs[0].dtype == torch.float64 else F32
+    for x, y in zip(xs, ys):
+        assert x.dtype == y.dtype == xs[0].dtype and x.is_cuda and y.is_cuda
+    H = (C.c_void_p * k)(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    X = (C.c_void_p * k)(*[x.data_ptr() for x in xs])
+    Y = (C.c_void_p * k)(*[y.data_ptr() for y in ys])
+    LD = (C.c_int64 * k)(*[int(v) for v in lds])
+    _check(lib().nnca_matvec_batch(H, k, X, Y, LD, nrhs, dtype, precision, _stream_ptr(stream)), None)
 
 
 def nnca_matvec_noalloc(handle, x, y, ld: int, precision: int = PREC_FP64, stream=None):

@@ -21,6 +21,12 @@ Workload recipes (all seeded with numpy's default_rng):
                      h = 0.2, ACA tolerance 1e-6, 64 right-hand sides: the
                      Gaussian kernel of the SVM experiment (Sec. 5.6).
 
+* ``batch32``      : 32 independent problems, N_k log-uniform in
+                     [16,384; 524,288], points uniform in [0, 1]^3, 16 with
+                     K = 1/r and 16 with K = exp(-r^2 / (2 h^2)), h = 0.2,
+                     ACA tolerance 1e-6, 8 right-hand sides x ~ N(0, 1)
+                     (batched uneven problems; ``batch_workloads``).
+
 The paper's experiments are all synthetic; no dataset stands behind them.
 """
 from __future__ import annotations
@@ -123,3 +129,18 @@ WORKLOADS = {
     "gauss_mix_256k": Workload("gauss_mix_256k", 1 << 18, 3, K_GAUSS, (1.0, 0.2, 1.0, 0.0), 64, 1e-6, 64,
                                4000, "gauss_mix", "normal", "8-Gaussian mixture, Gaussian kernel h = 0.2"),
 }
+
+
+def batch_workloads(count: int = 32, seed: int = 5000, n_lo: int = 1 << 14, n_hi: int = 1 << 19,
+                    nrhs: int = 8) -> list:
+    """The ``batch32`` recipe: ``count`` problems with sizes log-uniform in [n_lo, n_hi],
+    the first half with K = 1/r, the second half with the Gaussian kernel (h = 0.2)."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=count)).astype(np.int64)
+    out = []
+    for k, n in enumerate(sizes):
+        gauss = k >= count // 2
+        out.append(Workload(f"batch32[{k}]", int(n), 3, K_GAUSS if gauss else K_INV_R,
+                            (1.0, 0.2, 1.0, 0.0) if gauss else (1.0, 0.0, 0.0, 0.0), 64, 1e-6, nrhs, seed + 10 * (k + 1),
+                            "uniform_01", "normal", "batched uneven problems"))
+    return out

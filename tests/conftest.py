@@ -18,3 +18,15 @@ def orc():
     from oracle import oracle as O
     O.build()
     return O
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """The CUDA library's binding; skips without a CUDA device."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_14832_gb300 import _build, nnca
+    _build.build()
+    nnca.lib()
+    return nnca

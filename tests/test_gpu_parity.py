@@ -18,17 +18,6 @@ STRUCT = ["PERM", "KEYS", "LEVEL_BASE", "CKEY", "CBEG", "CEND", "CPAR", "CCH_BEG
           "IL_OFF", "IL_IDX"]
 
 
-@pytest.fixture(scope="module")
-def gpu():
-    torch = pytest.importorskip("torch")
-    if not torch.cuda.is_available():
-        pytest.skip("no CUDA device")
-    from paper_2203_14832_gb300 import _build, nnca
-    _build.build()
-    nnca.lib()
-    return nnca
-
-
 def configs(gpu, orc, w, **kw):
     c = dict(d=w.d, leaf_size=w.leaf_size, aca_tol=w.aca_tol, kernel=w.kernel, kparam=w.kparam)
     c.update(kw)
