@@ -21,6 +21,15 @@ Workload recipes (all seeded with numpy's default_rng):
                      h = 0.2, ACA tolerance 1e-6, 64 right-hand sides: the
                      Gaussian kernel of the SVM experiment (Sec. 5.6).
 
+* ``cheb2d_102k``  : the 320 x 320 tensor-product Chebyshev grid on [-1, 1]^2,
+                     kernel (i) of the experiments with a = 1e-4, leaf size 64,
+                     ACA tolerance 1e-9, x ~ N(0, 1) (Sec. 5, Experiment 2).
+* ``cheb3d_262k``  : the 64^3 tensor-product Chebyshev grid on [-1, 1]^3,
+                     kernel (ii) with a = 1e-4, ACA tolerance 1e-7 (Experiment 4).
+* ``fredholm3d_262k``: the 64^3 cell-centred uniform grid on [-1, 1]^3 and the
+                     Nystrom matrix of the second-kind equation of Experiment 5:
+                     A = I + h^3 K with K = 1/r off the diagonal (h = 2/64),
+                     ACA tolerance 1e-7; sigma ~ N(0, 1), f = A sigma.
 * ``batch32``      : 32 independent problems, N_k log-uniform in
                      [16,384; 524,288], points uniform in [0, 1]^3, 16 with
                      K = 1/r and 16 with K = exp(-r^2 / (2 h^2)), h = 0.2,
@@ -62,6 +71,21 @@ def chebyshev_grid(m: int, d: int) -> np.ndarray:
     return np.stack([g.ravel() for g in grids], axis=1)
 
 
+def uniform_grid(m: int, d: int) -> np.ndarray:
+    """Cell-centred uniform grid on [-1, 1]^d, m points per dimension."""
+    t = -1.0 + (np.arange(m) + 0.5) * (2.0 / m)
+    grids = np.meshgrid(*([t] * d), indexing="ij")
+    return np.stack([g.ravel() for g in grids], axis=1)
+
+
+def grid_side(n: int, d: int) -> int:
+    """m with m^d = n (grids are given by their point count)."""
+    m = int(round(n ** (1.0 / d)))
+    if m ** d != n:
+        raise ValueError(f"{n} points is not a {d}-dimensional grid")
+    return m
+
+
 def vector_uniform(n: int, seed: int, nrhs: int = 1) -> np.ndarray:
     v = np.random.default_rng(seed).uniform(-1.0, 1.0, size=(nrhs, n))
     return v[0] if nrhs == 1 else v
@@ -97,6 +121,10 @@ class Workload:
             return sphere_surface(n, self.seed)
         if self.points == "gauss_mix":
             return gaussian_mixture(n, self.d, self.seed)
+        if self.points == "chebyshev":
+            return chebyshev_grid(grid_side(n, self.d), self.d)
+        if self.points == "grid":
+            return uniform_grid(grid_side(n, self.d), self.d)
         raise ValueError(self.points)
 
     def make_vector(self, n: int | None = None) -> np.ndarray:
@@ -110,6 +138,8 @@ class Workload:
         kp = self.kparam
         if self.name.startswith("sphere"):
             kp = (sphere_weight(n),) + tuple(kp[1:])
+        if self.name.startswith("fredholm"):
+            kp = (nystrom_weight(n, self.d),) + tuple(kp[1:])
         return Workload(self.name + f"@{n}", n, self.d, self.kernel, kp, self.leaf_size, self.aca_tol,
                         self.nrhs, self.seed, self.points, self.vector, self.note)
 
@@ -119,6 +149,11 @@ def sphere_weight(n: int) -> float:
     return (1.0 / (4.0 * math.pi)) * (4.0 * math.pi / n)
 
 
+def nystrom_weight(n: int, d: int) -> float:
+    """Quadrature weight h^d of the cell-centred grid on [-1, 1]^d with n points."""
+    return (2.0 / grid_side(n, d)) ** d
+
+
 WORKLOADS = {
     "log2d_4096": Workload("log2d_4096", 4096, 2, K_LOG, (1.0, 0.0, 0.0, 0.0), 64, 1e-8, 1, 1000,
                            "uniform_pm1", "uniform", "2D uniform, log r, dense-checked"),
@@ -126,6 +161,12 @@ WORKLOADS = {
                           "uniform_01", "normal", "3D uniform, 1/r"),
     "sphere_512k": Workload("sphere_512k", 1 << 19, 3, K_INV_R, (sphere_weight(1 << 19), 0.0, 1.0, 0.0), 64,
                             1e-7, 1, 3000, "sphere", "normal", "unit sphere, 1/(4 pi r) * 4 pi / N"),
+    "cheb2d_102k": Workload("cheb2d_102k", 320 * 320, 2, K_PAPER_I, (1.0, 1e-4, 0.0, 0.0), 64, 1e-9, 1, 6000,
+                            "chebyshev", "normal", "2D Chebyshev grid, kernel (i), a = 1e-4"),
+    "cheb3d_262k": Workload("cheb3d_262k", 64 ** 3, 3, K_PAPER_II, (1.0, 1e-4, 0.0, 0.0), 64, 1e-7, 1, 7000,
+                            "chebyshev", "normal", "3D Chebyshev grid, kernel (ii), a = 1e-4"),
+    "fredholm3d_262k": Workload("fredholm3d_262k", 64 ** 3, 3, K_INV_R, ((2.0 / 64) ** 3, 0.0, 1.0, 0.0), 64, 1e-7, 1,
+                                8000, "grid", "normal", "Nystrom matrix I + h^3/r on the uniform grid"),
     "gauss_mix_256k": Workload("gauss_mix_256k", 1 << 18, 3, K_GAUSS, (1.0, 0.2, 1.0, 0.0), 64, 1e-6, 64,
                                4000, "gauss_mix", "normal", "8-Gaussian mixture, Gaussian kernel h = 0.2"),
 }
