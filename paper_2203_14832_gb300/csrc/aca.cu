@@ -913,8 +913,9 @@ __global__ void k_m2l_plan(int64_t np, const int32_t *parents, int d, int num, i
 // Points of every leaf for the FP32 near field, in pairs
 // [xh0 xh1 yh0 yh1][zh0 zh1 w0 w1][xl0 xl1 yl0 yl1][zl0 zl1 0 0]; padding points
 // far away with weight 0; weights 0 (each product writes its own). One warp per leaf.
-__global__ void k_pack_near(int64_t l0, int64_t l1, const int32_t *cbeg, const int32_t *cend, const int32_t *ppk_off,
-                            const float4 *xh4, const float4 *xl4, float4 *ppk) {
+__global__ void k_pack_near(int64_t l0, int64_t l1, int d, int64_t N, const int32_t *cbeg, const int32_t *cend,
+                            const int32_t *ppk_off, const float4 *xh4, const float4 *xl4, const float *xs32, float4 *ppk,
+                            float4 *ppl) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t c = l0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); c < l1; c += nw) {
@@ -929,16 +930,28 @@ __global__ void k_pack_near(int64_t l0, int64_t l1, const int32_t *cbeg, const i
             dst[1] = make_float4(h0.z, h1.z, 0.f, 0.f);
             dst[2] = make_float4(o0.x, o1.x, o0.y, o1.y);
             dst[3] = make_float4(o0.z, o1.z, 0.f, 0.f);
+            // relative to the leaf centre (the FP64 difference rounded once)
+            float a[2][3];
+            for (int e = 0; e < 2; ++e)
+                for (int k = 0; k < 3; ++k)
+                    a[e][k] = 2 * q + e < n ? (k < d ? xs32[(int64_t)k * N + i0 + 2 * q + e] : 0.f) : FAR_AWAY;
+            float4 *dl = ppl + 2 * (q0 + q);
+            dl[0] = make_float4(a[0][0], a[1][0], a[0][1], a[1][1]);
+            dl[1] = make_float4(a[0][2], a[1][2], 0.f, 0.f);
         }
     }
 }
 
 // Staging plan of the FP32 near field for leaf X: the leaves Y of N(X) (Table 1),
-// with a flag for X itself, cut greedily into rounds of at most NEAR_RECS cells
-// and NEAR_CAP point pairs. PASS 0 counts the records, PASS 1 writes them.
+// with flags for X itself and for leaves adjacent to X (integer offset at most 1
+// in every coordinate: their points can be arbitrarily close to X's and travel
+// as hi/lo pairs, 64 bytes per point pair; the others travel in their leaf's
+// frame, 32 bytes), cut greedily into rounds of at most NEAR_RECS cells and
+// NEAR_UNITS 16-byte units. PASS 0 counts the records, PASS 1 writes them.
 template <int PASS>
-__global__ void k_near_plan(int64_t l0, int64_t l1, const int32_t *nb_off, const int32_t *nb_idx,
-                            const int32_t *ppk_off, const int64_t *rec_off, int64_t *rec_cnt, int4 *rec) {
+__global__ void k_near_plan(int64_t l0, int64_t l1, int d, const int32_t *ccoord, int64_t ncell,
+                            const int32_t *nb_off, const int32_t *nb_idx, const int32_t *ppk_off,
+                            const int64_t *rec_off, int64_t *rec_cnt, int4 *rec) {
     for (int64_t X = l0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; X < l1; X += (int64_t)gridDim.x * blockDim.x) {
         int4 *out = PASS ? rec + rec_off[X - l0] : nullptr;
         int64_t n = 0, first = 0;
@@ -947,14 +960,20 @@ __global__ void k_near_plan(int64_t l0, int64_t l1, const int32_t *nb_off, const
             const int Y = nb_idx[q];
             const int np = ppk_off[Y + 1] - ppk_off[Y];
             if (np == 0) continue;
-            if (nr == NEAR_RECS || used + np > NEAR_CAP) {
+            int adj = 1;
+            for (int k = 0; k < d; ++k) {
+                const int t = ccoord[(int64_t)k * ncell + X] - ccoord[(int64_t)k * ncell + Y];
+                if (t > 1 || t < -1) adj = 0;
+            }
+            const int units = np * (adj ? 4 : 2);
+            if (nr == NEAR_RECS || used + units > NEAR_UNITS) {
                 if (PASS) out[first].w = nr;
                 first = n;
                 used = 0;
                 nr = 0;
             }
-            if (PASS) out[n] = make_int4(Y, ppk_off[Y], used | (np << 11) | ((Y == X ? 1 : 0) << 22), 0);
-            used += np;
+            if (PASS) out[n] = make_int4(Y, ppk_off[Y], used | (np << 11) | ((Y == X ? 1 : 0) << 22) | (adj << 23), 0);
+            used += units;
             ++nr;
             ++n;
         }
@@ -1256,12 +1275,13 @@ void build_finish(Handle *h) {
             h->ppk_off = dalloc<int32_t>(h, nc + 1);
             NNCA_CUDA(cudaMemcpy(h->ppk_off, hpk.data(), (nc + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
             h->ppk = dalloc<float4>(h, 4 * (size_t)npairs);
-            k_pack_near<<<grid_for(h->nleaf * 32, 256), 256, 0, s>>>(leaf0, leaf1, h->cbeg, h->cend, h->ppk_off, h->xh4,
-                                                                     h->xl4, h->ppk);
+            h->ppl = dalloc<float4>(h, 2 * (size_t)npairs);
+            k_pack_near<<<grid_for(h->nleaf * 32, 256), 256, 0, s>>>(leaf0, leaf1, d, N, h->cbeg, h->cend, h->ppk_off,
+                                                                     h->xh4, h->xl4, h->xs32, h->ppk, h->ppl);
             NNCA_LAUNCH_CHECK();
             int64_t *dcnt = scr.get<int64_t>(h->nleaf), *doff = scr.get<int64_t>(h->nleaf);
-            k_near_plan<0><<<grid_for(h->nleaf, 128), 128, 0, s>>>(leaf0, leaf1, h->nb_off, h->nb_idx, h->ppk_off,
-                                                                   nullptr, dcnt, nullptr);
+            k_near_plan<0><<<grid_for(h->nleaf, 128), 128, 0, s>>>(leaf0, leaf1, d, h->ccoord, nc, h->nb_off, h->nb_idx,
+                                                                   h->ppk_off, nullptr, dcnt, nullptr);
             NNCA_LAUNCH_CHECK();
             std::vector<int64_t> hcnt(h->nleaf), roff(h->nleaf + 1, 0);
             NNCA_CUDA(cudaMemcpy(hcnt.data(), dcnt, h->nleaf * sizeof(int64_t), cudaMemcpyDeviceToHost));
@@ -1270,8 +1290,8 @@ void build_finish(Handle *h) {
             h->n_near_plan = roff[h->nleaf];
             h->near_plan = dalloc<int4>(h, roff[h->nleaf]);
             NNCA_CUDA(cudaMemcpy(doff, roff.data(), h->nleaf * sizeof(int64_t), cudaMemcpyHostToDevice));
-            k_near_plan<1><<<grid_for(h->nleaf, 128), 128, 0, s>>>(leaf0, leaf1, h->nb_off, h->nb_idx, h->ppk_off, doff,
-                                                                   nullptr, h->near_plan);
+            k_near_plan<1><<<grid_for(h->nleaf, 128), 128, 0, s>>>(leaf0, leaf1, d, h->ccoord, nc, h->nb_off, h->nb_idx,
+                                                                   h->ppk_off, doff, nullptr, h->near_plan);
             NNCA_LAUNCH_CHECK();
             // items: one leaf each; its c targets sit TPL (2 or 3) per lane on
             // L = ceil(c / TPL) lanes, and G = floor(32 / L) groups of L lanes

@@ -116,10 +116,11 @@ unsigned grid_for(int64_t n, int threads, int64_t cap = 152 * 64) {
 
 // ---- permutation into tree order --------------------------------------------
 // FP32 product (one right-hand side): also the float weight slot of each point
-// in the packed near-field pairs (leaf Y, local index j: pair ppk_off[Y] + j/2)
+// in the packed near-field pairs, hi/lo and local (leaf Y, local index j: pair
+// ppk_off[Y] + j/2)
 template <class TI>
 __global__ void k_perm_in(const TI *x, int64_t ld, int64_t N, int64_t nrhs, const int32_t *perm, double *xt,
-                          float *xt32, float *ppk_w, const int32_t *leaf_of, const int32_t *cbeg,
+                          float *xt32, float *ppk_w, float *ppl_w, const int32_t *leaf_of, const int32_t *cbeg,
                           const int32_t *ppk_off) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N * nrhs; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = e / N, i = e - r * N;
@@ -130,6 +131,7 @@ __global__ void k_perm_in(const TI *x, int64_t ld, int64_t N, int64_t nrhs, cons
             const int Y = leaf_of[i];
             const int64_t j = i - cbeg[Y];
             ppk_w[((int64_t)ppk_off[Y] + (j >> 1)) * 16 + 6 + (j & 1)] = (float)v;
+            ppl_w[((int64_t)ppk_off[Y] + (j >> 1)) * 8 + 6 + (j & 1)] = (float)v;
         }
     }
 }
@@ -942,20 +944,27 @@ __global__ void __launch_bounds__(32 * MV_WARPS) k_leaf_f32(KParams kp, const in
     }
 }
 
-// ---- leaves: L2P (FP64) + P2P (FP32, hi/lo coordinates), one warp per leaf -------
+// ---- leaves: L2P (FP64) + P2P (FP32), one warp per leaf ------------------------------
 // A warp serves the c targets of one leaf: TPL consecutive targets per lane on
 // L = ceil(c / TPL) lanes, and G = floor(32 / L) groups of L lanes that split
 // the source pairs of every cell (the layout is chosen per leaf at build time
 // to leave few target slots idle). The points of N(B) arrive by bulk
-// asynchronous copies (TMA), one per cell, from the packed point pairs into
-// NEAR_BUFS buffers of the warp, each tracked by its own mbarrier; the warp
-// stages up to two rounds ahead of its evaluation, so no other warp takes part.
-// Each cell is summed in float and added into a compensated total; pairs of B
-// with itself are guarded against r = 0 (the diagonal takes the configured
-// value afterwards).
+// asynchronous copies (TMA), one per cell, into NEAR_BUFS buffers of the warp,
+// each tracked by its own mbarrier; the warp stages up to two rounds ahead of
+// its evaluation, so no other warp takes part. Leaves adjacent to B (offset at
+// most 1 in every coordinate) hold points that can come arbitrarily close to
+// B's: they travel as absolute hi/lo pairs and every difference is formed as
+// (hi_s - hi_t) + (lo_s - lo_t). The other leaves of N(B) are at least one leaf
+// away: they travel relative to their own centre c_Y, and each target moves
+// into that frame once per cell, t - c_Y = (hi_t - hi_c) + (lo_t - lo_c). Each
+// cell is summed in float and added into a compensated total; pairs of B with
+// itself are guarded against r = 0 (the diagonal takes the configured value
+// afterwards).
 struct NearWarpSmem {
-    float4 src[NEAR_BUFS][NEAR_CAP][4];   // point pairs: hi xy, hi z + weights, lo xy, lo z
-    int hdr[NEAR_BUFS][NEAR_RECS];        // slot | pairs << 11 | own leaf << 22
+    float4 u[NEAR_BUFS][NEAR_UNITS];      // staged points: hi/lo pairs (4 units) or local pairs (2 units)
+    int hdr[NEAR_BUFS][NEAR_RECS];        // slot | pairs << 11 | own leaf << 22 | adjacent << 23
+    float4 ch[NEAR_BUFS][NEAR_RECS];      // centre of the cell as float hi
+    float4 cl[NEAR_BUFS][NEAR_RECS];      // and lo
     int nrec[NEAR_BUFS];
     unsigned long long full[NEAR_BUFS];   // mbarriers
 };
@@ -993,19 +1002,41 @@ __device__ __forceinline__ f2 near_pair(const KParams &kp, const ulonglong2 &A, 
     return f2_fma(KF2<KIND, SAFE>::eval(kp, r2), B.y, acc);
 }
 
-// Stage the round of plan records held by the warp (lane i: record k + i) into buffer b.
-__device__ __forceinline__ int near_stage(NearWarpSmem &W, int b, const int4 &r, int k, int kend, const float4 *ppk,
-                                          unsigned *status) {
+// The staging warp's copy of the next round's plan records (lane i: record k + i)
+// and of the records' cell centres, loaded one round ahead.
+struct NearCursor {
+    int4 r = make_int4(0, 0, 0, 0);
+    float4 ch = make_float4(0.f, 0.f, 0.f, 0.f), cl = make_float4(0.f, 0.f, 0.f, 0.f);
+};
+
+__device__ __forceinline__ void near_load(NearCursor &c, const int4 *plan, const float4 *chi, const float4 *clo, int k,
+                                          int kend) {
     const int lane = threadIdx.x & 31;
-    const int nrec = __shfl_sync(0xffffffffu, r.w, 0);
+    if (k + lane < kend) {
+        c.r = plan[k + lane];
+        c.ch = chi[c.r.x];
+        c.cl = clo[c.r.x];
+    }
+}
+
+// Stage the round held by the cursor into buffer b.
+__device__ __forceinline__ int near_stage(NearWarpSmem &W, int b, const NearCursor &c, int k, int kend,
+                                          const float4 *ppk, const float4 *ppl, unsigned *status) {
+    const int lane = threadIdx.x & 31;
+    const int nrec = __shfl_sync(0xffffffffu, c.r.w, 0);
     if (nrec < 1 || nrec > NEAR_RECS || k + nrec > kend) {   // a malformed plan: stop, never spin
         if (lane == 0) atomicOr(status, DEV_BAD_INDEX);
         return -1;
     }
     unsigned bytes = 0;
+    const float4 *src = nullptr;
     if (lane < nrec) {
-        W.hdr[b][lane] = r.z;
-        bytes = (unsigned)((r.z >> 11) & 0x7ff) * 64u;
+        const int adj = (c.r.z >> 23) & 1, np = (c.r.z >> 11) & 0x7ff;
+        W.hdr[b][lane] = c.r.z;
+        W.ch[b][lane] = c.ch;
+        W.cl[b][lane] = c.cl;
+        bytes = (unsigned)np * (adj ? 64u : 32u);
+        src = adj ? ppk + 4 * (int64_t)c.r.y : ppl + 2 * (int64_t)c.r.y;
     }
     const unsigned total = __reduce_add_sync(0xffffffffu, bytes);
     if (lane == 0) W.nrec[b] = nrec;
@@ -1014,33 +1045,73 @@ __device__ __forceinline__ int near_stage(NearWarpSmem &W, int b, const int4 &r,
     __syncwarp();
     if (lane == 0) mbar_arrive_tx(&W.full[b], total);
     __syncwarp();
-    if (lane < nrec) bulk_g2s(&W.src[b][r.z & 0x7ff][0], ppk + 4 * (int64_t)r.y, bytes, &W.full[b]);
+    if (lane < nrec) bulk_g2s(&W.u[b][c.r.z & 0x7ff], src, bytes, &W.full[b]);
     return k + nrec;
 }
 
-// one cell: this lane's group takes source pairs q0 + g, q0 + g + G, ...
+// an adjacent cell (hi/lo pairs at P[4 q]): this lane's group takes pairs g, g + G, ...
 template <int KIND, int TPL, bool SAFE>
-__device__ __forceinline__ void near_cell(const KParams &kp, const NearWarpSmem &W, int b, int q0, int q1, int g,
-                                          int G, NearTarget (&T)[TPL]) {
+__device__ __forceinline__ void near_cell(const KParams &kp, const float4 *P, int np, int g, int G,
+                                          NearTarget (&T)[TPL]) {
     f2 acc[TPL][2];
 #pragma unroll
     for (int k = 0; k < TPL; ++k) acc[k][0] = acc[k][1] = 0ull;
-    for (int q = q0 + g; q < q1; q += 2 * G) {
+    for (int q = g; q < np; q += 2 * G) {
         {
-            const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(&W.src[b][q][0]);
-            const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(&W.src[b][q][1]);
-            const ulonglong2 C = *reinterpret_cast<const ulonglong2 *>(&W.src[b][q][2]);
-            const ulonglong2 D = *reinterpret_cast<const ulonglong2 *>(&W.src[b][q][3]);
+            const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(&P[4 * q]);
+            const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(&P[4 * q + 1]);
+            const ulonglong2 C = *reinterpret_cast<const ulonglong2 *>(&P[4 * q + 2]);
+            const ulonglong2 D = *reinterpret_cast<const ulonglong2 *>(&P[4 * q + 3]);
 #pragma unroll
             for (int k = 0; k < TPL; ++k) acc[k][0] = near_pair<KIND, SAFE>(kp, A, B, C, D, T[k], acc[k][0]);
         }
-        if (q + G < q1) {
-            const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(&W.src[b][q + G][0]);
-            const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(&W.src[b][q + G][1]);
-            const ulonglong2 C = *reinterpret_cast<const ulonglong2 *>(&W.src[b][q + G][2]);
-            const ulonglong2 D = *reinterpret_cast<const ulonglong2 *>(&W.src[b][q + G][3]);
+        if (q + G < np) {
+            const int q2 = q + G;
+            const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(&P[4 * q2]);
+            const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(&P[4 * q2 + 1]);
+            const ulonglong2 C = *reinterpret_cast<const ulonglong2 *>(&P[4 * q2 + 2]);
+            const ulonglong2 D = *reinterpret_cast<const ulonglong2 *>(&P[4 * q2 + 3]);
 #pragma unroll
             for (int k = 0; k < TPL; ++k) acc[k][1] = near_pair<KIND, SAFE>(kp, A, B, C, D, T[k], acc[k][1]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < TPL; ++k) {
+        const float2 p = f2_unpack(f2_add(acc[k][0], acc[k][1]));
+        two_sum_add(T[k].sum, T[k].comp, p.x + p.y);
+    }
+}
+
+// a leaf at least one leaf away (pairs relative to its centre at P[2 q]): the
+// targets move into its frame once, then one packed difference per coordinate
+template <int KIND, int TPL>
+__device__ __forceinline__ void near_cell_far(const KParams &kp, const float4 *P, int np, int g, int G, float4 ch,
+                                              float4 cl, NearTarget (&T)[TPL]) {
+    f2 tx[TPL], ty[TPL], tz[TPL], acc[TPL][2];
+    {
+        const f2 hx = f2_pack(ch.x, ch.x), hy = f2_pack(ch.y, ch.y), hz = f2_pack(ch.z, ch.z);
+        const f2 lx = f2_pack(cl.x, cl.x), ly = f2_pack(cl.y, cl.y), lz = f2_pack(cl.z, cl.z);
+#pragma unroll
+        for (int k = 0; k < TPL; ++k) {
+            tx[k] = f2_add(f2_sub(T[k].xh, hx), f2_sub(T[k].xl, lx));
+            ty[k] = f2_add(f2_sub(T[k].yh, hy), f2_sub(T[k].yl, ly));
+            tz[k] = f2_add(f2_sub(T[k].zh, hz), f2_sub(T[k].zl, lz));
+            acc[k][0] = acc[k][1] = 0ull;
+        }
+    }
+    for (int q = g; q < np; q += 2 * G) {
+        {
+            const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(&P[2 * q]);
+            const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(&P[2 * q + 1]);
+#pragma unroll
+            for (int k = 0; k < TPL; ++k) acc[k][0] = group_pair<KIND>(kp, A, B, tx[k], ty[k], tz[k], acc[k][0]);
+        }
+        if (q + G < np) {
+            const int q2 = q + G;
+            const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(&P[2 * q2]);
+            const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(&P[2 * q2 + 1]);
+#pragma unroll
+            for (int k = 0; k < TPL; ++k) acc[k][1] = group_pair<KIND>(kp, A, B, tx[k], ty[k], tz[k], acc[k][1]);
         }
     }
 #pragma unroll
@@ -1055,7 +1126,8 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_near_group(KParams kp, cons
                                                                int *next_item, const int4 *plan, const int32_t *cbeg,
                                                                const int32_t *piv_off, const int64_t *op_off,
                                                                const double *op, const double *u, const float4 *xh4,
-                                                               const float4 *xl4, const float4 *ppk,
+                                                               const float4 *xl4, const float4 *chi, const float4 *clo,
+                                                               const float4 *ppk, const float4 *ppl,
                                                                const double *xt64, const int32_t *perm, TO *y,
                                                                unsigned *status) {
     __shared__ __align__(128) NearWarpSmem Sm[NEAR_WARPS];
@@ -1084,12 +1156,12 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_near_group(KParams kp, cons
 #pragma unroll
         for (int k = 0; k < TPL; ++k) near_target(T[k], live && ti * TPL + k < c, i0 + ti * TPL + k, xh4, xl4);
         int kprod = item.z, kcons = item.z;
-        int4 rec = make_int4(0, 0, 0, 0);
-        if (kprod + lane < kend) rec = plan[kprod + lane];
+        NearCursor cur;
+        near_load(cur, plan, chi, clo, kprod, kend);
         while (kcons < kend) {
             // stage up to two rounds beyond the one evaluated (the third buffer is free)
             while (kprod < kend && Rp <= R + NEAR_BUFS - 2) {
-                const int kn = near_stage(W, Rp % NEAR_BUFS, rec, kprod, kend, ppk, status);
+                const int kn = near_stage(W, Rp % NEAR_BUFS, cur, kprod, kend, ppk, ppl, status);
                 if (kn < 0) {
                     kprod = kend;
                     failed = true;
@@ -1097,7 +1169,7 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_near_group(KParams kp, cons
                 }
                 kprod = kn;
                 ++Rp;
-                if (kprod + lane < kend) rec = plan[kprod + lane];
+                near_load(cur, plan, chi, clo, kprod, kend);
             }
             if (failed) break;
             const int b = R % NEAR_BUFS;
@@ -1110,9 +1182,11 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_near_group(KParams kp, cons
             if (live)
                 for (int e = 0; e < nrec; ++e) {
                     const int hw = W.hdr[b][e];
-                    const int q0 = hw & 0x7ff, q1 = q0 + ((hw >> 11) & 0x7ff);
-                    if ((hw >> 22) & 1) near_cell<KIND, TPL, true>(kp, W, b, q0, q1, g, G, T);
-                    else near_cell<KIND, TPL, false>(kp, W, b, q0, q1, g, G, T);
+                    const float4 *P = &W.u[b][hw & 0x7ff];
+                    const int np = (hw >> 11) & 0x7ff;
+                    if (!((hw >> 23) & 1)) near_cell_far<KIND, TPL>(kp, P, np, g, G, W.ch[b][e], W.cl[b][e], T);
+                    else if ((hw >> 22) & 1) near_cell<KIND, TPL, true>(kp, P, np, g, G, T);
+                    else near_cell<KIND, TPL, false>(kp, P, np, g, G, T);
                 }
             __syncwarp();
             ++R;
@@ -1326,7 +1400,7 @@ void launch_leaf_f32(Handle *h, const double *op, const double *u, const float *
         const unsigned g = (unsigned)((std::min<int64_t>(n, warps) + NEAR_WARPS - 1) / NEAR_WARPS);                    \
         k_near_group<KIND, TPL, TO><<<g, 32 * NEAR_WARPS, 0, h->stream>>>(                                             \
             h->kp, h->near_items[t], n, h->near_next + t, h->near_plan, h->cbeg, h->piv_off, h->op_off, op, u, h->xh4, \
-            h->xl4, h->ppk, xt64, h->perm, y, h->dev_status);                                                          \
+            h->xl4, h->chi4, h->clo4, h->ppk, h->ppl, xt64, h->perm, y, h->dev_status);                                \
     } while (0)
             if (t == 0) NNCA_NEAR(2);
             else NNCA_NEAR(3);
@@ -1385,8 +1459,9 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
     TO *yout = (TO *)y + r0 * ld;
     prof_mark(h, 0);
     float *ppk_w = FP32 && kernel_is_radial(h->kp.kind) && h->near_packed ? reinterpret_cast<float *>(h->ppk) : nullptr;
-    k_perm_in<TO><<<grid_for(N * NR, 256), 256, 0, s>>>(xin, ld, N, NR, h->perm, xt, xt32, ppk_w, h->leaf_of, h->cbeg,
-                                                        h->ppk_off);
+    float *ppl_w = ppk_w ? reinterpret_cast<float *>(h->ppl) : nullptr;
+    k_perm_in<TO><<<grid_for(N * NR, 256), 256, 0, s>>>(xin, ld, N, NR, h->perm, xt, xt32, ppk_w, ppl_w, h->leaf_of,
+                                                        h->cbeg, h->ppk_off);
     NNCA_LAUNCH_CHECK();
     ++h->launches;
     prof_mark(h, 1);

@@ -176,8 +176,9 @@ constexpr int M2L_STAGE_BUFS = 4;
 // most NEAR_RECS cells and NEAR_CAP point pairs through NEAR_BUFS buffers per
 // warp, which bounds the largest leaf it takes (2 * NEAR_CAP points).
 constexpr int NEAR_WARPS = 4;
-constexpr int NEAR_CAP = 48;
-constexpr int NEAR_RECS = 32;
+constexpr int NEAR_CAP = 48;                  // point pairs of hi/lo coordinates per buffer
+constexpr int NEAR_UNITS = 4 * NEAR_CAP;      // buffer size in 16-byte units
+constexpr int NEAR_RECS = 16;
 constexpr int NEAR_BUFS = 3;
 // coordinate of a padding source: far from every target, weight 0
 constexpr float FAR_AWAY = 1.0e18f;
@@ -272,11 +273,12 @@ struct Handle {
     // [xl0 xl1 yl0 yl1][zl0 zl1 0 0] (absolute coordinates as float hi + lo,
     // padded to m2l_padded(points) with far-away points of weight 0; the
     // products write the weights) from pair ppk_off[cell]; per-leaf staging plans
-    // (cell, first pair, slot | pairs << 11 | own leaf << 22, cells in the round
-    // or 0) and items (leaf, first target | targets << 16 | groups << 24, first
+    // (cell, first pair, slot in 16-byte units | pairs << 11 | own leaf << 22 |
+    // adjacent << 23, cells in the round or 0) and items (leaf, first target | targets << 16 | groups << 24, first
     // record, records) for 2 and 3 targets per lane
     float4 *ppk = nullptr;
-    int32_t *ppk_off = nullptr;   // [ncell + 1]
+    float4 *ppl = nullptr;        // the same points as [x0 x1 y0 y1][z0 z1 w0 w1] relative to the leaf centre
+    int32_t *ppk_off = nullptr;   // [ncell + 1], pairs (the same for ppk and ppl)
     int4 *near_plan = nullptr;
     int64_t n_near_plan = 0;
     int4 *near_items[2] = {nullptr, nullptr};   // by targets per lane (2, 3)

@@ -107,3 +107,25 @@ def test_leaf_size_tuner(gpu):
     assert float(torch.linalg.norm(y - y2) / torch.linalg.norm(y2)) < 50 * w.aca_tol
     h.close()
     h2.close()
+
+
+@pytest.mark.gpu
+def test_autograd_in_x(gpu, orc):
+    """dL/dx of L = <w, A x> is A^T w = A w (symmetric); against the oracle's dense product."""
+    import torch
+    from paper_2203_14832_gb300.autograd import h2_matvec
+    w = W.WORKLOADS["invr3d_1m"].scaled(6000)
+    P = w.make_points()
+    cfg = gpu.Config(d=3, leaf_size=32, aca_tol=1e-8, kernel=w.kernel, kparam=w.kparam)
+    h = gpu.H2(torch.as_tensor(P, device="cuda"), cfg)
+    x = torch.as_tensor(w.make_vector(), device="cuda").requires_grad_(True)
+    wt = torch.as_tensor(W.vector_normal(w.n, 77), device="cuda")
+    y = h2_matvec(h, x)
+    (wt * y).sum().backward()
+    ocfg = orc.Config(d=3, leaf_size=32, aca_tol=1e-8, kernel=w.kernel, kparam=w.kparam)
+    gd = orc.dense_matvec(P, wt.cpu().numpy(), ocfg)
+    g = x.grad.cpu().numpy()
+    assert np.linalg.norm(g - gd) / np.linalg.norm(gd) < 1e-6
+    # the gradient is the same handle's product on w, bit for bit
+    assert torch.equal(x.grad, h.matvec(wt))
+    h.close()
