@@ -1246,17 +1246,83 @@ void build_finish(Handle *h) {
                                                            h->m2l_plan_sh);
             NNCA_LAUNCH_CHECK();
         }
-        std::vector<int4> v;
+        // Items, heaviest first. An item whose pairs (targets x staged sources)
+        // exceed a share of the whole that one block of a full wave would carry
+        // (total / (4 * 5 * SMs)) is cut at staging-round boundaries into pieces of
+        // about equal work, so that no single block holds the launch's tail.
+        std::vector<int4> hplan(h->n_m2l_plan);
+        if (h->n_m2l_plan)
+            NNCA_CUDA(cudaMemcpy(hplan.data(), h->m2l_plan, h->n_m2l_plan * sizeof(int4), cudaMemcpyDeviceToHost));
+        struct Round { int k, n; int64_t src; };
+        std::vector<std::vector<Round>> rounds(np);
+        for (int64_t i = 0; i < np && h->n_m2l_plan; ++i)
+            for (int64_t k = roff[i]; k < roff[i + 1];) {
+                const int nrec = hplan[k].w;
+                NNCA_REQUIRE(nrec >= 1 && k + nrec <= roff[i + 1], NNCA_ERR_INTERNAL, "malformed M2L staging plan");
+                int64_t src = 0;
+                for (int e = 0; e < nrec; ++e) src += 2 * ((hplan[k + e].z >> 11) & 0x7ff);
+                rounds[i].push_back({(int)k, nrec, src});
+                k += nrec;
+            }
+        int dev = 0, nsm = 152;
+        NNCA_CUDA(cudaGetDevice(&dev));
+        NNCA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        int64_t total = 0;
+        for (auto &g : groups)
+            for (auto &r : rounds[g.parent_slot]) total += (int64_t)g.nt * r.src;
+        const int64_t wmax = std::max<int64_t>(1, total / ((int64_t)nsm * 5 * 4));
+        struct Piece { int64_t weight; int4 item; int part; };
+        std::vector<Piece> pieces;
+        std::vector<int4> splits;
+        int nparts = 0;
         for (auto &g : groups) {
             const int P = parents[g.parent_slot];
-            v.push_back(make_int4(P, g.t0 | (g.nt << 16), (int)roff[g.parent_slot],
-                                  (int)(roff[g.parent_slot + 1] - roff[g.parent_slot])));
+            const auto &R = rounds[g.parent_slot];
+            int64_t wsum = 0;
+            for (auto &r : R) wsum += (int64_t)g.nt * r.src;
+            const int64_t want = std::min<int64_t>((int64_t)R.size(), std::max<int64_t>(1, (wsum + wmax - 1) / wmax));
+            if (want <= 1) {
+                pieces.push_back({wsum, make_int4(P, g.t0 | (g.nt << 16), (int)roff[g.parent_slot],
+                                                  (int)(roff[g.parent_slot + 1] - roff[g.parent_slot])), -1});
+                continue;
+            }
+            const int first = nparts;
+            int64_t acc = 0, cut = 0;
+            size_t r0 = 0;
+            for (size_t r = 0; r < R.size(); ++r) {
+                acc += (int64_t)g.nt * R[r].src;
+                const bool last = r + 1 == R.size();
+                if (last || acc * want >= (cut + 1) * wsum) {
+                    const int k0 = R[r0].k, k1 = R[r].k + R[r].n;
+                    int64_t wp = 0;
+                    for (size_t q = r0; q <= r; ++q) wp += (int64_t)g.nt * R[q].src;
+                    pieces.push_back({wp, make_int4(P, g.t0 | (g.nt << 16), k0, k1 - k0), nparts++});
+                    r0 = r + 1;
+                    ++cut;
+                }
+            }
+            splits.push_back(make_int4((int)(hpo[hchb[P]] + g.t0), g.nt, first, nparts - first));
+        }
+        std::stable_sort(pieces.begin(), pieces.end(), [](const Piece &x, const Piece &y) { return x.weight > y.weight; });
+        std::vector<int4> v;
+        std::vector<int> vp;
+        for (auto &p : pieces) {
+            v.push_back(p.item);
+            vp.push_back(p.part);
         }
         h->n_m2l_groups = (int)v.size();
         h->m2l_groups = dalloc<int4>(h, v.size());
+        h->m2l_item_part = dalloc<int>(h, vp.size());
         h->m2l_next = dalloc<int>(h, 1);
-        if (!v.empty())
+        if (!v.empty()) {
             NNCA_CUDA(cudaMemcpy(h->m2l_groups, v.data(), v.size() * sizeof(int4), cudaMemcpyHostToDevice));
+            NNCA_CUDA(cudaMemcpy(h->m2l_item_part, vp.data(), vp.size() * sizeof(int), cudaMemcpyHostToDevice));
+        }
+        h->n_m2l_split = (int)splits.size();
+        h->m2l_split = dalloc<int4>(h, splits.size());
+        h->m2l_parts = dalloc<double>(h, (size_t)std::max(nparts, 1) * M2L_GROUP_TARGETS);
+        if (!splits.empty())
+            NNCA_CUDA(cudaMemcpy(h->m2l_split, splits.data(), splits.size() * sizeof(int4), cudaMemcpyHostToDevice));
         NNCA_CUDA(cudaStreamSynchronize(s));
     }
     {

@@ -728,7 +728,8 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group(KParams kp, con
                                                                const int32_t *cch_beg, const int32_t *cch_end,
                                                                const int2 *prange, const float4 *pv4,
                                                                const float4 *chi, const float4 *clo,
-                                                               const float4 *spk, double *u, unsigned *status) {
+                                                               const float4 *spk, const int *item_part,
+                                                               double *parts, double *u, unsigned *status) {
     __shared__ __align__(128) M2lGroupSmem S;
     const int tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
     if (tid == 0) {
@@ -750,6 +751,7 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group(KParams kp, con
         const int it = S.item;
         if (it >= nitems || *(volatile int *)&S.abort) break;
         const int4 item = items[it];
+        const int part = item_part[it];   // -1: the whole item, else the slot of its partial sums
         const int P = item.x, t0 = item.y & 0xffff, nt = item.y >> 16, kend = item.z + item.w;
         const int cb = cch_beg[P], nch = cch_end[P] - cb;
         if (tid < nch) S.ch_range[tid] = prange[cb + tid];
@@ -829,8 +831,12 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group(KParams kp, con
                 Tb.comp += cb2;
             }
         }
-        if (grp == 0 && Ta.c < 31) u[Ta.g] = kp.s * ((double)Ta.sum + (double)Ta.comp);
-        if (grp == 0 && Tb.c < 31) u[Tb.g] = kp.s * ((double)Tb.sum + (double)Tb.comp);
+        if (grp == 0) {
+            const int gb = S.ch_range[0].x + t0;   // pivot of the item's first target
+            double *dst = part < 0 ? u + gb : parts + (int64_t)part * M2L_GROUP_TARGETS;
+            if (Ta.c < 31) dst[Ta.g - gb] = kp.s * ((double)Ta.sum + (double)Ta.comp);
+            if (Tb.c < 31) dst[Tb.g - gb] = kp.s * ((double)Tb.sum + (double)Tb.comp);
+        }
     }
     // after a timed-out wait: let copies still in flight land before the block exits
     if (wl == pw && lane == 0)
@@ -1366,6 +1372,18 @@ __global__ void k_leaf_generic(KParams kp, int d, const int32_t *leaves, int64_t
 }
 
 // ---- launch helpers ----------------------------------------------------------
+// u of the targets of a split item: the sum of its pieces' partial sums, in piece order
+__global__ void k_m2l_combine(const int4 *split, int nsplit, const double *parts, double *u) {
+    for (int i = blockIdx.x; i < nsplit; i += gridDim.x) {
+        const int4 sp = split[i];   // first pivot, targets, first slot, pieces
+        for (int j = threadIdx.x; j < sp.y; j += blockDim.x) {
+            double v = 0.0;
+            for (int p = 0; p < sp.w; ++p) v += parts[(int64_t)(sp.z + p) * M2L_GROUP_TARGETS + j];
+            u[sp.x + j] = v;
+        }
+    }
+}
+
 template <int KIND>
 void launch_m2l_f32(Handle *h, double *u) {
     if (!h->n_m2l_groups) return;
@@ -1377,9 +1395,16 @@ void launch_m2l_f32(Handle *h, double *u) {
     NNCA_CUDA(cudaMemsetAsync(h->m2l_next, 0, sizeof(int), h->stream));
     k_m2l_group<KIND><<<g, M2L_GROUP_THREADS, 0, h->stream>>>(h->kp, h->m2l_groups, h->n_m2l_groups, h->m2l_next,
                                                              h->m2l_plan, h->m2l_plan_sh, h->cch_beg, h->cch_end, h->prange, h->pv4,
-                                                             h->chi4, h->clo4, h->spk, u, h->dev_status);
+                                                             h->chi4, h->clo4, h->spk, h->m2l_item_part, h->m2l_parts, u,
+                                                             h->dev_status);
     NNCA_LAUNCH_CHECK();
     ++h->launches;
+    if (h->n_m2l_split) {
+        k_m2l_combine<<<(unsigned)std::min(h->n_m2l_split, 152 * 16), 256, 0, h->stream>>>(h->m2l_split, h->n_m2l_split,
+                                                                                          h->m2l_parts, u);
+        NNCA_LAUNCH_CHECK();
+        ++h->launches;
+    }
 }
 
 template <int KIND, class TO>

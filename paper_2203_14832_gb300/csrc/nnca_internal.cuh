@@ -269,6 +269,13 @@ struct Handle {
     int4 *m2l_groups = nullptr;
     int n_m2l_groups = 0;
     int *m2l_next = nullptr;      // item counter of the FP32 M2L launch
+    // heavy items are split at staging-round boundaries: such a piece writes
+    // its partial sums to m2l_parts[slot][0, targets), and a combine pass adds the
+    // pieces of each split (u offset, targets, first slot, pieces) in order
+    int *m2l_item_part = nullptr;   // per item: part slot, or -1 (writes u)
+    double *m2l_parts = nullptr;
+    int4 *m2l_split = nullptr;
+    int n_m2l_split = 0;
     // FP32 near field: points of every leaf as pairs [xh0 xh1 yh0 yh1][zh0 zh1 w0 w1]
     // [xl0 xl1 yl0 yl1][zl0 zl1 0 0] (absolute coordinates as float hi + lo,
     // padded to m2l_padded(points) with far-away points of weight 0; the
