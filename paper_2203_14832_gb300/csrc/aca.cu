@@ -833,21 +833,28 @@ __global__ void k_pack_points(int64_t n, int64_t npiv, int d, const double *xs, 
 }
 
 // Sources of every cell for the FP32 M2L, in pairs [x0 x1 y0 y1][z0 z1 w0 w1]
-// relative to the cell centre; padding sources far away; weights 0 (each
-// product writes its own). One warp per cell.
-__global__ void k_pack_sources(int64_t nc, const int2 *prange, const int32_t *spk_off, const float4 *pv4,
-                               float4 *spk) {
+// relative to the centre of the cell's PARENT (so that sibling cells share a
+// frame and consecutive siblings can be evaluated as one segment; the FP64
+// difference rounded once); padding sources far away; weights 0 (each product
+// writes its own). One warp per cell; the root has no sources in the M2L.
+__global__ void k_pack_sources(int64_t nc, int d, int64_t npiv, const int2 *prange, const int32_t *spk_off,
+                               const int32_t *cpar, const double *pv64, const double *ccen, float4 *spk) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < nc; c += nw) {
         const int2 pr = prange[c];
         const int64_t q0 = spk_off[c], nq = spk_off[c + 1] - q0;
+        const int64_t Q = c > 0 ? cpar[c] : 0;
         for (int64_t q = lane; q < nq; q += 32) {
-            const float4 far4 = make_float4(FAR_AWAY, FAR_AWAY, FAR_AWAY, 0.f);
-            const float4 v0 = 2 * q < pr.y ? pv4[pr.x + 2 * q] : far4;
-            const float4 v1 = 2 * q + 1 < pr.y ? pv4[pr.x + 2 * q + 1] : far4;
-            spk[2 * (q0 + q)] = make_float4(v0.x, v1.x, v0.y, v1.y);
-            spk[2 * (q0 + q) + 1] = make_float4(v0.z, v1.z, 0.f, 0.f);
+            float a[2][3];
+            for (int e = 0; e < 2; ++e)
+                for (int k = 0; k < 3; ++k)
+                    a[e][k] = 2 * q + e < pr.y
+                                  ? (k < d ? (float)(pv64[(int64_t)k * npiv + pr.x + 2 * q + e] - ccen[(int64_t)k * nc + Q])
+                                           : 0.f)
+                                  : FAR_AWAY;
+            spk[2 * (q0 + q)] = make_float4(a[0][0], a[1][0], a[0][1], a[1][1]);
+            spk[2 * (q0 + q) + 1] = make_float4(a[0][2], a[1][2], 0.f, 0.f);
         }
     }
 }
@@ -855,8 +862,10 @@ __global__ void k_pack_sources(int64_t nc, const int2 *prange, const int32_t *sp
 // Staging plan of the FP32 M2L for parent P (Table 1): the children Y of N(P)
 // with sources, each with the mask of P's children that admit it (the test of
 // the list construction, so the mask bit of child X is set exactly when Y is
-// in IL(X)), cut greedily into rounds of at most M2L_STAGE_RECS cells and
-// M2L_STAGE_CAP padded sources. PASS 0 counts the records, PASS 1 writes them.
+// in IL(X)), cut greedily into rounds of at most M2L_STAGE_RECS records and
+// M2L_STAGE_CAP padded sources. Consecutive siblings (one parent Q, adjacent
+// cell ids, so adjacent packed sources) with the same mask share one record
+// and the shift c_Q - c_P. PASS 0 counts the records, PASS 1 writes them.
 template <int PASS>
 __global__ void k_m2l_plan(int64_t np, const int32_t *parents, int d, int num, int den, const int32_t *ccoord,
                            int64_t ncell, const int32_t *cch_beg, const int32_t *cch_end, const int32_t *nb_off,
@@ -867,7 +876,7 @@ __global__ void k_m2l_plan(int64_t np, const int32_t *parents, int d, int num, i
         const int cb = cch_beg[P], nch = cch_end[P] - cb;
         int4 *out = PASS ? rec + rec_off[i] : nullptr;
         int64_t n = 0, first = 0;
-        int used = 0, nr = 0;
+        int used = 0, nr = 0, last_y = -2, last_mask = -1, last_q = -1;
         for (int q = nb_off[P]; q < nb_off[P + 1]; ++q) {
             const int Q = nb_idx[q];
             for (int y = cch_beg[Q]; y < cch_end[Q]; ++y) {
@@ -887,6 +896,13 @@ __global__ void k_m2l_plan(int64_t np, const int32_t *parents, int d, int num, i
                 }
                 if (!mask) continue;
                 const int npad = m2l_padded(rank);
+                if (nr > 0 && Q == last_q && y == last_y + 1 && mask == last_mask && used + npad <= M2L_STAGE_CAP) {
+                    // the next sibling with the same mask extends the last record
+                    if (PASS) out[n - 1].z += (npad >> 1) << 11;
+                    used += npad;
+                    last_y = y;
+                    continue;
+                }
                 if (nr == M2L_STAGE_RECS || used + npad > M2L_STAGE_CAP) {
                     if (PASS) out[first].w = nr;
                     first = n;
@@ -895,14 +911,17 @@ __global__ void k_m2l_plan(int64_t np, const int32_t *parents, int d, int num, i
                 }
                 if (PASS) {
                     out[n] = make_int4(y, spk_off[y], (used >> 1) | ((npad >> 1) << 11) | (mask << 22), 0);
-                    // c_Y - c_P, the FP64 difference rounded once
+                    // c_Q - c_P for the parent Q of y, the FP64 difference rounded once
                     float sh[3] = {0.f, 0.f, 0.f};
-                    for (int k = 0; k < d && k < 3; ++k) sh[k] = (float)(ccen[(int64_t)k * ncell + y] - ccen[(int64_t)k * ncell + P]);
+                    for (int k = 0; k < d && k < 3; ++k) sh[k] = (float)(ccen[(int64_t)k * ncell + Q] - ccen[(int64_t)k * ncell + P]);
                     rec_sh[rec_off[i] + n] = make_float4(sh[0], sh[1], sh[2], 0.f);
                 }
                 used += npad;
                 ++nr;
                 ++n;
+                last_y = y;
+                last_mask = mask;
+                last_q = Q;
             }
         }
         if (PASS && nr > 0) out[first].w = nr;
@@ -1186,7 +1205,8 @@ void build_finish(Handle *h) {
         h->spk_off = dalloc<int32_t>(h, nc + 1);
         NNCA_CUDA(cudaMemcpy(h->spk_off, hso.data(), (nc + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
         h->spk = dalloc<float4>(h, 2 * (size_t)npairs);
-        k_pack_sources<<<grid_for(nc * 32, 256), 256, 0, s>>>(nc, h->prange, h->spk_off, h->pv4, h->spk);
+        k_pack_sources<<<grid_for(nc * 32, 256), 256, 0, s>>>(nc, d, h->npiv, h->prange, h->spk_off, h->cpar, h->pv64,
+                                                              h->ccen, h->spk);
         NNCA_LAUNCH_CHECK();
 
         // M2L items: the targets of one parent's children (their pivots are

@@ -558,6 +558,7 @@ __device__ __forceinline__ void unpack_item(int2 it, int &cell, int &a0, int &c)
 constexpr int M2L_GROUP_THREADS = 32 * M2L_GROUP_WARPS;
 
 constexpr int M2L_STAGE_AHEAD = M2L_STAGE_BUFS - 2;
+constexpr int M2L_FOLD = 8;   // couples of source pairs per lane between folds into the compensated totals
 
 struct M2lGroupSmem {
     float4 src[M2L_STAGE_BUFS][M2L_STAGE_CAP / 2][2];   // staged source pairs
@@ -803,15 +804,22 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group(KParams kp, con
                     const f2 xa = f2_sub(Ta.tx, SX), ya = f2_sub(Ta.ty, SY), za = f2_sub(Ta.tz, SZ);
                     const f2 xb = f2_sub(Tb.tx, SX), yb = f2_sub(Tb.ty, SY), zb = f2_sub(Tb.tz, SZ);
                     const int q0 = hw & 0x7ff, q1 = q0 + ((hw >> 11) & 0x7ff);
-                    f2 a0 = 0ull, a1 = 0ull, b0 = 0ull, b1 = 0ull;
-                    if (G == 1)
-                        m2l_cell_pairs<KIND, 1>(kp, S.src[b], q0, q1, xa, ya, za, xb, yb, zb, a0, a1, b0, b1);
-                    else
-                        m2l_cell_pairs<KIND, 0>(kp, S.src[b], q0 + 2 * grp, q1, xa, ya, za, xb, yb, zb, a0, a1, b0, b1,
-                                                2 * G);
-                    const float2 pa = f2_unpack(f2_add(a0, a1)), pb = f2_unpack(f2_add(b0, b1));
-                    if ((m >> Ta.c) & 1u) two_sum_add(Ta.sum, Ta.comp, pa.x + pa.y);
-                    if ((m >> Tb.c) & 1u) two_sum_add(Tb.sum, Tb.comp, pb.x + pb.y);
+                    const bool ona = (m >> Ta.c) & 1u, onb = (m >> Tb.c) & 1u;
+                    // a segment (one cell or a run of siblings) in chunks of M2L_FOLD couples of
+                    // pairs per lane, each chunk folded into the compensated totals
+                    const int span = 2 * M2L_FOLD * G;
+                    for (int c0 = q0; c0 < q1; c0 += span) {
+                        const int c1 = min(q1, c0 + span);
+                        f2 a0 = 0ull, a1 = 0ull, b0 = 0ull, b1 = 0ull;
+                        if (G == 1)
+                            m2l_cell_pairs<KIND, 1>(kp, S.src[b], c0, c1, xa, ya, za, xb, yb, zb, a0, a1, b0, b1);
+                        else
+                            m2l_cell_pairs<KIND, 0>(kp, S.src[b], c0 + 2 * grp, c1, xa, ya, za, xb, yb, zb, a0, a1, b0,
+                                                    b1, 2 * G);
+                        const float2 pa = f2_unpack(f2_add(a0, a1)), pb = f2_unpack(f2_add(b0, b1));
+                        if (ona) two_sum_add(Ta.sum, Ta.comp, pa.x + pa.y);
+                        if (onb) two_sum_add(Tb.sum, Tb.comp, pb.x + pb.y);
+                    }
                 }
             }
             __syncwarp();
