@@ -1205,6 +1205,8 @@ void build_finish(Handle *h) {
         h->spk_off = dalloc<int32_t>(h, nc + 1);
         NNCA_CUDA(cudaMemcpy(h->spk_off, hso.data(), (nc + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
         h->spk = dalloc<float4>(h, 2 * (size_t)npairs);
+        h->spw = dalloc<float4>(h, (M2L_RHS / 2) * (size_t)npairs);
+        NNCA_CUDA(cudaMemsetAsync(h->spw, 0, (M2L_RHS / 2) * (size_t)npairs * sizeof(float4), s));
         k_pack_sources<<<grid_for(nc * 32, 256), 256, 0, s>>>(nc, d, h->npiv, h->prange, h->spk_off, h->cpar, h->pv64,
                                                               h->ccen, h->spk);
         NNCA_LAUNCH_CHECK();
@@ -1340,7 +1342,7 @@ void build_finish(Handle *h) {
         }
         h->n_m2l_split = (int)splits.size();
         h->m2l_split = dalloc<int4>(h, splits.size());
-        h->m2l_parts = dalloc<double>(h, (size_t)std::max(nparts, 1) * M2L_GROUP_TARGETS);
+        h->m2l_parts = dalloc<double>(h, (size_t)std::max(nparts, 1) * M2L_GROUP_TARGETS * M2L_RHS);
         if (!splits.empty())
             NNCA_CUDA(cudaMemcpy(h->m2l_split, splits.data(), splits.size() * sizeof(int4), cudaMemcpyHostToDevice));
         NNCA_CUDA(cudaStreamSynchronize(s));

@@ -136,6 +136,19 @@ __global__ void k_perm_in(const TI *x, int64_t ld, int64_t N, int64_t nrhs, cons
     }
 }
 
+// FP32 product, one right-hand side of a multi-RHS pass: its float weights into
+// the packed near-field pairs (hi/lo and local)
+__global__ void k_near_weights(int64_t N, const double *xt, float *ppk_w, float *ppl_w, const int32_t *leaf_of,
+                               const int32_t *cbeg, const int32_t *ppk_off) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int Y = leaf_of[i];
+        const int64_t j = i - cbeg[Y];
+        const float v = (float)xt[i];
+        ppk_w[((int64_t)ppk_off[Y] + (j >> 1)) * 16 + 6 + (j & 1)] = v;
+        ppl_w[((int64_t)ppk_off[Y] + (j >> 1)) * 8 + 6 + (j & 1)] = v;
+    }
+}
+
 // ---- P2M / M2M and L2L: batched small products with the FP64 operators --------
 // The operators of the upper levels are few and large (hundreds of rows), those
 // of the leaves many and small, so a team of TW warps serves one cell and each
@@ -153,7 +166,8 @@ __global__ void __launch_bounds__(UP_THREADS) k_upward(int64_t b0, int64_t b1, i
                                                       const int32_t *cend, const int32_t *cch_beg,
                                                       const int32_t *cch_end, const int32_t *piv_off,
                                                       const int64_t *op_off, const T *op, const T *xt, int64_t N,
-                                                      T *w, int64_t npiv, float *spk_w, const int32_t *spk_off) {
+                                                      T *w, int64_t npiv, float *spk_w, const int32_t *spk_off,
+                                                      float *spw = nullptr) {
     constexpr int TEAMS = UP_THREADS / (32 * TW);
     constexpr int CH = TW == 1 ? 64 : UP_CHUNK;   // rows staged per chunk
     __shared__ T sv[TEAMS][NR][CH];
@@ -238,6 +252,12 @@ __global__ void __launch_bounds__(UP_THREADS) k_upward(int64_t b0, int64_t b1, i
                 for (int q = 0; q < NR; ++q) w[q * npiv + piv_off[B] + b] = acc[q];
                 // FP32 product: the weight slot of pivot b in the packed sources
                 if (spk_w) spk_w[((int64_t)spk_off[B] + (b >> 1)) * 8 + 6 + (b & 1)] = (float)acc[0];
+                // FP32 product with M2L_RHS right-hand sides: the packed weights of each
+                if (spw && NR == M2L_RHS)
+#pragma unroll
+                    for (int q = 0; q < NR; ++q)
+                        spw[((int64_t)spk_off[B] + (b >> 1)) * (2 * M2L_RHS) + (q >> 1) * 4 + (q & 1) * 2 + (b & 1)] =
+                            (float)acc[q];
             }
         }
     }
@@ -559,6 +579,7 @@ constexpr int M2L_GROUP_THREADS = 32 * M2L_GROUP_WARPS;
 
 constexpr int M2L_STAGE_AHEAD = M2L_STAGE_BUFS - 2;
 constexpr int M2L_FOLD = 8;   // couples of source pairs per lane between folds into the compensated totals
+constexpr int M2L_FOLD_RHS = 4;   // the same with M2L_RHS right-hand sides (one chain per right-hand side)
 
 struct M2lGroupSmem {
     float4 src[M2L_STAGE_BUFS][M2L_STAGE_CAP / 2][2];   // staged source pairs
@@ -1380,14 +1401,234 @@ __global__ void k_leaf_generic(KParams kp, int d, const int32_t *leaves, int64_t
 }
 
 // ---- launch helpers ----------------------------------------------------------
+// ---- M2L, FP32 evaluation, M2L_RHS right-hand sides per pass ---------------------------
+// The same staging and evaluation as k_m2l_group; every round also brings the
+// cells' weights of the M2L_RHS right-hand sides (a second bulk copy per record),
+// and each kernel value f(|s - t|) feeds M2L_RHS accumulators, so the geometry
+// and the MUFU work of a pair serve all of them.
+struct M2lRhsSmem {
+    float4 src[M2L_STAGE_BUFS][M2L_STAGE_CAP / 2][2];             // source pairs (coordinates)
+    float4 wt[M2L_STAGE_BUFS][M2L_STAGE_CAP / 2][M2L_RHS / 2];    // their weights, two right-hand sides per float4
+    int hdr[M2L_STAGE_BUFS][M2L_STAGE_RECS];
+    float4 sh[M2L_STAGE_BUFS][M2L_STAGE_RECS];
+    int nrec[M2L_STAGE_BUFS];
+    unsigned long long full[M2L_STAGE_BUFS], empty[M2L_STAGE_BUFS];
+    int2 ch_range[8];
+    int item;
+    int abort;
+};
+
+__device__ __forceinline__ int m2l_stage_rhs(M2lRhsSmem &S, int b, unsigned use, StageCursor &cur, const int4 *plan,
+                                             const float4 *plan_sh, int kend, const float4 *spk, const float4 *spw,
+                                             unsigned *status) {
+    const int lane = threadIdx.x & 31;
+    if (use > 0 && !mbar_wait_warp(&S.empty[b], (use - 1) & 1)) {
+        if (lane == 0) {
+            atomicOr(status, DEV_WAIT_TIMEOUT);
+            *(volatile int *)&S.abort = 1;
+        }
+        return kend;
+    }
+    const int k = cur.k;
+    const int nrec = __shfl_sync(0xffffffffu, cur.r.w, 0);
+    if (nrec < 1 || nrec > M2L_STAGE_RECS || k + nrec > kend) {   // a malformed plan: stop, never spin
+        if (lane == 0) {
+            atomicOr(status, DEV_BAD_INDEX);
+            *(volatile int *)&S.abort = 1;
+        }
+        return kend;
+    }
+    unsigned bytes = 0;
+    const int4 r = cur.r;
+    const unsigned np = (unsigned)((r.z >> 11) & 0x7ff);
+    if (lane < nrec) {
+        S.hdr[b][lane] = r.z;
+        S.sh[b][lane] = cur.sh;
+        bytes = np * 32u + np * (unsigned)(16 * (M2L_RHS / 2));
+    }
+    const unsigned total = __reduce_add_sync(0xffffffffu, bytes);
+    if (lane == 0) S.nrec[b] = nrec;
+    __syncwarp();
+    if (lane == 0) mbar_arrive_tx(&S.full[b], total);
+    __syncwarp();
+    if (lane < nrec) {
+        bulk_g2s(&S.src[b][r.z & 0x7ff][0], spk + 2 * (int64_t)r.y, np * 32u, &S.full[b]);
+        bulk_g2s(&S.wt[b][r.z & 0x7ff][0], spw + (M2L_RHS / 2) * (int64_t)r.y, np * (unsigned)(16 * (M2L_RHS / 2)),
+                 &S.full[b]);
+    }
+    if (k + nrec < kend) stage_load(cur, plan, plan_sh, k + nrec, kend);
+    return k + nrec;
+}
+
+// f(|s - t|^2) of a packed pair of sources
+template <int KIND>
+__device__ __forceinline__ f2 group_f(const KParams &kp, const ulonglong2 &A, const ulonglong2 &B, f2 tx, f2 ty, f2 tz) {
+    const f2 dx = f2_sub(A.x, tx), dy = f2_sub(A.y, ty), dz = f2_sub(B.x, tz);
+    f2 r2 = f2_mul(dx, dx);
+    r2 = f2_fma(dy, dy, r2);
+    r2 = f2_fma(dz, dz, r2);
+    return KF2<KIND, false>::eval(kp, r2);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group_rhs(KParams kp, const int4 *items, int nitems,
+                                                                   int *next_item, const int4 *plan,
+                                                                   const float4 *plan_sh, const int32_t *cch_beg,
+                                                                   const int32_t *cch_end, const int2 *prange,
+                                                                   const float4 *pv4, const float4 *chi,
+                                                                   const float4 *clo, const float4 *spk,
+                                                                   const float4 *spw, const int *item_part,
+                                                                   double *parts, double *u, int64_t npiv,
+                                                                   unsigned *status) {
+    extern __shared__ __align__(128) unsigned char m2l_rhs_smem[];
+    M2lRhsSmem &S = *reinterpret_cast<M2lRhsSmem *>(m2l_rhs_smem);
+    const int tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
+    if (tid == 0) {
+        for (int b = 0; b < M2L_STAGE_BUFS; ++b) {
+            mbar_init(&S.full[b], 1);
+            mbar_init(&S.empty[b], M2L_GROUP_WARPS);
+        }
+        S.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const int pw = blockIdx.x % M2L_GROUP_WARPS;
+    unsigned R = 0, Rp = 0;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) S.item = atomicAdd(next_item, 1);
+        __syncthreads();
+        const int it = S.item;
+        if (it >= nitems || *(volatile int *)&S.abort) break;
+        const int4 item = items[it];
+        const int part = item_part[it];
+        const int P = item.x, t0 = item.y & 0xffff, nt = item.y >> 16, kend = item.z + item.w;
+        const int cb = cch_beg[P], nch = cch_end[P] - cb;
+        if (tid < nch) S.ch_range[tid] = prange[cb + tid];
+        __syncthreads();
+        const float4 hP = chi[P], lP = clo[P];
+        int kprod = item.z, kcons = item.z;
+        StageCursor cur;
+        if (wl == pw && kprod < kend) stage_load(cur, plan, plan_sh, kprod, kend);
+        const int wj0 = t0 + wl * M2L_WARP_TARGETS, jend = t0 + nt;
+        const int cw = min(M2L_WARP_TARGETS, max(0, jend - wj0));
+        const int L = cw > 0 ? (cw + 1) / 2 : 32;
+        const int G = min(16, 32 / L);
+        const int grp = lane / L, ti = lane - grp * L;
+        const bool live = grp < G;
+        const int j = wj0 + 2 * ti;
+        const int g = S.ch_range[0].x + j;
+        GroupTarget Ta, Tb;
+        group_target(Ta, live && j < jend, g, nch, cb, S.ch_range, pv4, chi, clo, hP, lP);
+        group_target(Tb, live && j + 1 < jend, g + 1, nch, cb, S.ch_range, pv4, chi, clo, hP, lP);
+        float sa[M2L_RHS], ca[M2L_RHS], sb[M2L_RHS], cbm[M2L_RHS];
+#pragma unroll
+        for (int r = 0; r < M2L_RHS; ++r) sa[r] = ca[r] = sb[r] = cbm[r] = 0.f;
+        const unsigned omask =
+            __reduce_or_sync(0xffffffffu, (Ta.c < 31 ? 1u << Ta.c : 0u) | (Tb.c < 31 ? 1u << Tb.c : 0u));
+        while (kcons < kend) {
+            if (wl == pw)
+                while (kprod < kend && Rp <= R + M2L_STAGE_AHEAD) {
+                    kprod = m2l_stage_rhs(S, Rp % M2L_STAGE_BUFS, Rp / M2L_STAGE_BUFS, cur, plan, plan_sh, kend, spk,
+                                          spw, status);
+                    ++Rp;
+                }
+            const int b = R % M2L_STAGE_BUFS;
+            if (!mbar_wait_warp(&S.full[b], (R / M2L_STAGE_BUFS) & 1)) {
+                if (lane == 0) {
+                    atomicOr(status, DEV_WAIT_TIMEOUT);
+                    *(volatile int *)&S.abort = 1;
+                }
+                break;
+            }
+            const int nrec = S.nrec[b];
+            if (nrec < 1) break;   // unreachable with a well-formed plan
+            if (omask && live) {
+                for (int i = 0; i < nrec; ++i) {
+                    const int hw = S.hdr[b][i];
+                    const unsigned m = ((unsigned)hw >> 22) & omask;
+                    if (!m) continue;
+                    const float4 sh = S.sh[b][i];
+                    const f2 SX = f2_pack(sh.x, sh.x), SY = f2_pack(sh.y, sh.y), SZ = f2_pack(sh.z, sh.z);
+                    const f2 xa = f2_sub(Ta.tx, SX), ya = f2_sub(Ta.ty, SY), za = f2_sub(Ta.tz, SZ);
+                    const f2 xb = f2_sub(Tb.tx, SX), yb = f2_sub(Tb.ty, SY), zb = f2_sub(Tb.tz, SZ);
+                    const int q0 = hw & 0x7ff, q1 = q0 + ((hw >> 11) & 0x7ff);
+                    const bool ona = (m >> Ta.c) & 1u, onb = (m >> Tb.c) & 1u;
+                    const int span = 2 * M2L_FOLD_RHS * G;
+                    for (int c0 = q0; c0 < q1; c0 += span) {
+                        const int c1 = min(q1, c0 + span);
+                        f2 aa[M2L_RHS], ab[M2L_RHS];
+#pragma unroll
+                        for (int r = 0; r < M2L_RHS; ++r) aa[r] = ab[r] = 0ull;
+                        for (int q = c0 + (G == 1 ? 0 : 2 * grp); q < c1; q += 2 * G) {
+#pragma unroll
+                            for (int h2 = 0; h2 < 2; ++h2) {
+                                const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(&S.src[b][q + h2][0]);
+                                const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(&S.src[b][q + h2][1]);
+                                const f2 fa = group_f<KIND>(kp, A, B, xa, ya, za);
+                                const f2 fb = group_f<KIND>(kp, A, B, xb, yb, zb);
+#pragma unroll
+                                for (int r2 = 0; r2 < M2L_RHS / 2; ++r2) {
+                                    const ulonglong2 W = *reinterpret_cast<const ulonglong2 *>(&S.wt[b][q + h2][r2]);
+                                    aa[2 * r2] = f2_fma(fa, W.x, aa[2 * r2]);
+                                    aa[2 * r2 + 1] = f2_fma(fa, W.y, aa[2 * r2 + 1]);
+                                    ab[2 * r2] = f2_fma(fb, W.x, ab[2 * r2]);
+                                    ab[2 * r2 + 1] = f2_fma(fb, W.y, ab[2 * r2 + 1]);
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int r = 0; r < M2L_RHS; ++r) {
+                            const float2 pa = f2_unpack(aa[r]), pb = f2_unpack(ab[r]);
+                            if (ona) two_sum_add(sa[r], ca[r], pa.x + pa.y);
+                            if (onb) two_sum_add(sb[r], cbm[r], pb.x + pb.y);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.empty[b]);
+            ++R;
+            kcons += nrec;
+        }
+        // the groups summed disjoint source pairs of the same targets: combine into group 0
+        for (int gg = 1; gg < G; ++gg) {
+            const int srcl = min(ti + gg * L, 31);
+#pragma unroll
+            for (int r = 0; r < M2L_RHS; ++r) {
+                const float x1 = __shfl_sync(0xffffffffu, sa[r], srcl), y1 = __shfl_sync(0xffffffffu, ca[r], srcl);
+                const float x2 = __shfl_sync(0xffffffffu, sb[r], srcl), y2 = __shfl_sync(0xffffffffu, cbm[r], srcl);
+                if (grp == 0) {
+                    two_sum_add(sa[r], ca[r], x1);
+                    ca[r] += y1;
+                    two_sum_add(sb[r], cbm[r], x2);
+                    cbm[r] += y2;
+                }
+            }
+        }
+        if (grp == 0) {
+            const int gb = S.ch_range[0].x + t0;
+#pragma unroll
+            for (int r = 0; r < M2L_RHS; ++r) {
+                double *dst = part < 0 ? u + r * npiv + gb : parts + ((int64_t)part * M2L_RHS + r) * M2L_GROUP_TARGETS;
+                if (Ta.c < 31) dst[Ta.g - gb] = kp.s * ((double)sa[r] + (double)ca[r]);
+                if (Tb.c < 31) dst[Tb.g - gb] = kp.s * ((double)sb[r] + (double)cbm[r]);
+            }
+        }
+    }
+    if (wl == pw && lane == 0)
+        for (unsigned r = R; r < Rp; ++r) mbar_wait(&S.full[r % M2L_STAGE_BUFS], (r / M2L_STAGE_BUFS) & 1);
+}
+
 // u of the targets of a split item: the sum of its pieces' partial sums, in piece order
-__global__ void k_m2l_combine(const int4 *split, int nsplit, const double *parts, double *u) {
+// (nr right-hand sides: slot s holds nr consecutive rows of M2L_GROUP_TARGETS)
+__global__ void k_m2l_combine(const int4 *split, int nsplit, const double *parts, double *u, int nr, int64_t npiv) {
     for (int i = blockIdx.x; i < nsplit; i += gridDim.x) {
         const int4 sp = split[i];   // first pivot, targets, first slot, pieces
-        for (int j = threadIdx.x; j < sp.y; j += blockDim.x) {
+        for (int e = threadIdx.x; e < sp.y * nr; e += blockDim.x) {
+            const int r = e / sp.y, j = e - r * sp.y;
             double v = 0.0;
-            for (int p = 0; p < sp.w; ++p) v += parts[(int64_t)(sp.z + p) * M2L_GROUP_TARGETS + j];
-            u[sp.x + j] = v;
+            for (int p = 0; p < sp.w; ++p) v += parts[((int64_t)(sp.z + p) * nr + r) * M2L_GROUP_TARGETS + j];
+            u[r * npiv + sp.x + j] = v;
         }
     }
 }
@@ -1409,7 +1650,32 @@ void launch_m2l_f32(Handle *h, double *u) {
     ++h->launches;
     if (h->n_m2l_split) {
         k_m2l_combine<<<(unsigned)std::min(h->n_m2l_split, 152 * 16), 256, 0, h->stream>>>(h->m2l_split, h->n_m2l_split,
-                                                                                          h->m2l_parts, u);
+                                                                                          h->m2l_parts, u, 1, h->npiv);
+        NNCA_LAUNCH_CHECK();
+        ++h->launches;
+    }
+}
+
+// M2L_RHS right-hand sides at once (u: M2L_RHS rows of npiv)
+template <int KIND>
+void launch_m2l_f32_rhs(Handle *h, double *u) {
+    if (!h->n_m2l_groups) return;
+    const int smem = (int)sizeof(M2lRhsSmem);
+    NNCA_CUDA(cudaFuncSetAttribute(k_m2l_group_rhs<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int dev = 0, nsm = 152, per_sm = 1;
+    NNCA_CUDA(cudaGetDevice(&dev));
+    NNCA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    NNCA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_m2l_group_rhs<KIND>, M2L_GROUP_THREADS, smem));
+    const unsigned g = (unsigned)std::min<int64_t>(h->n_m2l_groups, (int64_t)nsm * std::max(1, per_sm));
+    NNCA_CUDA(cudaMemsetAsync(h->m2l_next, 0, sizeof(int), h->stream));
+    k_m2l_group_rhs<KIND><<<g, M2L_GROUP_THREADS, smem, h->stream>>>(
+        h->kp, h->m2l_groups, h->n_m2l_groups, h->m2l_next, h->m2l_plan, h->m2l_plan_sh, h->cch_beg, h->cch_end,
+        h->prange, h->pv4, h->chi4, h->clo4, h->spk, h->spw, h->m2l_item_part, h->m2l_parts, u, h->npiv, h->dev_status);
+    NNCA_LAUNCH_CHECK();
+    ++h->launches;
+    if (h->n_m2l_split) {
+        k_m2l_combine<<<(unsigned)std::min(h->n_m2l_split, 152 * 16), 256, 0, h->stream>>>(
+            h->m2l_split, h->n_m2l_split, h->m2l_parts, u, M2L_RHS, h->npiv);
         NNCA_LAUNCH_CHECK();
         ++h->launches;
     }
@@ -1486,12 +1752,15 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
     double *w = xt + NR * N;
     double *u = w + NR * npiv;
     float *xt32 = FP32 ? (float *)(u + NR * npiv) : nullptr;
-    // FP32: the weights go straight into the packed M2L sources
-    float *spk_w = FP32 && kernel_is_radial(h->kp.kind) ? reinterpret_cast<float *>(h->spk) : nullptr;
+    // FP32: the weights go straight into the packed M2L sources (one right-hand
+    // side) or into the packed weights of an M2L_RHS pass
+    const bool f32 = FP32 && kernel_is_radial(h->kp.kind);
+    float *spk_w = f32 && NR == 1 ? reinterpret_cast<float *>(h->spk) : nullptr;
+    float *spw = f32 && NR == M2L_RHS ? reinterpret_cast<float *>(h->spw) : nullptr;
     const TO *xin = (const TO *)x + r0 * ld;
     TO *yout = (TO *)y + r0 * ld;
     prof_mark(h, 0);
-    float *ppk_w = FP32 && kernel_is_radial(h->kp.kind) && h->near_packed ? reinterpret_cast<float *>(h->ppk) : nullptr;
+    float *ppk_w = f32 && NR == 1 && h->near_packed ? reinterpret_cast<float *>(h->ppk) : nullptr;
     float *ppl_w = ppk_w ? reinterpret_cast<float *>(h->ppl) : nullptr;
     k_perm_in<TO><<<grid_for(N * NR, 256), 256, 0, s>>>(xin, ld, N, NR, h->perm, xt, xt32, ppk_w, ppl_w, h->leaf_of,
                                                         h->cbeg, h->ppk_off);
@@ -1504,7 +1773,7 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
         const int64_t lb = h->level_base[h->kappa], le = h->level_base[h->kappa + 1];
         k_upward<double, NR, 1><<<grid_for(le - lb, UP_THREADS / 32), UP_THREADS, 0, s>>>(lb, le, 1, h->cbeg, h->cend, h->cch_beg,
                                                                            h->cch_end, h->piv_off, h->op_off, op, xt,
-                                                                           N, w, npiv, spk_w, h->spk_off);
+                                                                           N, w, npiv, spk_w, h->spk_off, spw);
         NNCA_LAUNCH_CHECK();
         ++h->launches;
         for (int l = h->kappa - 1; l >= h->lmin; --l) {
@@ -1513,7 +1782,7 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
             k_upward<double, NR, UP_THREADS / 32><<<grid_for(b1 - b0, 1), UP_THREADS, 0, s>>>(b0, b1, 0, h->cbeg, h->cend,
                                                                                h->cch_beg, h->cch_end, h->piv_off,
                                                                                h->op_off, op, xt, N, w, npiv, spk_w,
-                                                                               h->spk_off);
+                                                                               h->spk_off, spw);
             NNCA_LAUNCH_CHECK();
         }
         prof_mark(h, 2);
@@ -1523,8 +1792,10 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
             if (!kernel_is_radial(h->kp.kind)) {
                 k_m2l_generic<NR><<<grid_for(h->n_m2l_tgt * 32, 128), 128, 0, s>>>(
                     h->kp, h->d, h->m2l_tgt, h->n_m2l_tgt, h->il_off, h->il_idx, h->piv_off, h->pv64, npiv, w, u);
-            } else if (FP32) {
+            } else if (FP32 && NR == 1) {
                 launch_m2l_f32<KIND>(h, u);
+            } else if (FP32 && NR == M2L_RHS) {
+                launch_m2l_f32_rhs<KIND>(h, u);
             } else {
                 k_m2l_f64<KIND, NR><<<g, 32 * MV_WARPS, 0, s>>>(h->kp, h->d, h->m2l_tgt, h->n_m2l_tgt, h->il_off,
                                                                 h->il_idx, h->piv_off, h->pv64, npiv, w, u);
@@ -1552,8 +1823,20 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
         k_leaf_generic<NR, TO><<<grid_for(h->nleaf * 32, 128), 128, 0, s>>>(
             h->kp, h->d, h->leaf_order, h->nleaf, h->cbeg, h->cend, h->nb_off, h->nb_idx, h->piv_off, h->op_off, op, u,
             npiv, h->xs, N, xt, h->perm, yout, ld);
-    } else if (FP32) {
+    } else if (FP32 && NR == 1) {
         launch_leaf_f32<KIND, TO>(h, op, u, xt32, xt, yout);
+    } else if (FP32) {
+        // the near field one right-hand side at a time
+        for (int r = 0; r < NR; ++r) {
+            if (h->near_packed) {
+                k_near_weights<<<grid_for(N, 256), 256, 0, s>>>(N, xt + r * N, reinterpret_cast<float *>(h->ppk),
+                                                                reinterpret_cast<float *>(h->ppl), h->leaf_of, h->cbeg,
+                                                                h->ppk_off);
+                NNCA_LAUNCH_CHECK();
+                ++h->launches;
+            }
+            launch_leaf_f32<KIND, TO>(h, op, u + r * npiv, xt32 + r * N, xt + r * N, yout + r * ld);
+        }
     } else {
         k_leaf_f64<KIND, NR, TO><<<gl, 32 * MV_WARPS, 0, s>>>(h->kp, h->d, h->leaf_order, h->nleaf, h->cbeg, h->cend,
                                                               h->nb_off, h->nb_idx, h->piv_off, h->op_off, op, u, npiv,
@@ -1567,7 +1850,7 @@ template <bool FP32, int KIND, class TO>
 void run_all(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld) {
     int64_t r0 = 0;
     while (r0 < nrhs) {
-        if (!FP32 && nrhs - r0 >= 4) {
+        if (nrhs - r0 >= 4) {
             run_chunk<FP32, 4, KIND, TO>(h, x, y, ld, r0);
             r0 += 4;
         } else {

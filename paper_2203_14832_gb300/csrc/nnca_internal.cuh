@@ -171,6 +171,9 @@ constexpr int M2L_GROUP_TARGETS = M2L_WARP_TARGETS * M2L_GROUP_WARPS;
 constexpr int M2L_STAGE_CAP = 512;
 constexpr int M2L_STAGE_RECS = 32;
 constexpr int M2L_STAGE_BUFS = 4;
+// right-hand sides of one FP32 M2L pass with several (their weights travel as
+// [w(2q, r) w(2q+1, r) w(2q, r+1) w(2q+1, r+1)] float4 pairs per source pair q)
+constexpr int M2L_RHS = 4;
 // The FP32 near field runs independent warps, NEAR_WARPS per block, one leaf
 // (up to 64 targets) per work item. The points of N(B) arrive in rounds of at
 // most NEAR_RECS cells and NEAR_CAP point pairs through NEAR_BUFS buffers per
@@ -298,6 +301,7 @@ struct Handle {
     int64_t n_m2l_plan = 0;
     float4 *spk = nullptr;
     int32_t *spk_off = nullptr;   // [ncell + 1]
+    float4 *spw = nullptr;        // [pairs][M2L_RHS / 2]: weights of a pass with M2L_RHS right-hand sides
     int64_t n_spk_pairs = 0;
     int2 *leaf_items[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int n_leaf_items[5] = {0, 0, 0, 0, 0};

@@ -261,3 +261,23 @@ def test_full_size_invr3d(gpu, orc):
     az = g.matvec(torch.as_tensor(z, device="cuda")).cpu().numpy()
     assert abs(x @ az - z @ y64) <= 1e-12 * np.linalg.norm(x) * np.linalg.norm(az)
     g.close()
+
+
+def test_fp32_multi_rhs(gpu, orc):
+    """FP32 form with 9 right-hand sides (two passes of four and one single): every column
+    within 1e-6 of the oracle's FP64 product and of the single-RHS FP32 product."""
+    import torch
+    w = W.WORKLOADS["invr3d_1m"].scaled(12000)
+    P = w.make_points()
+    gcfg, ocfg = configs(gpu, orc, w, leaf_size=32)
+    g = gpu.H2(torch.as_tensor(P, device="cuda"), gcfg)
+    o = orc.H2(P, ocfg)
+    X = W.vector_normal(12000, 21, nrhs=9)
+    Y32 = g.matvec(torch.as_tensor(X, device="cuda"), gpu.PREC_FP32).cpu().numpy()
+    for r in range(9):
+        yo = o.matvec(X[r].copy())
+        y1 = g.matvec(torch.as_tensor(X[r].copy(), device="cuda"), gpu.PREC_FP32).cpu().numpy()
+        assert rel(Y32[r], yo) < 1e-6
+        assert rel(Y32[r], y1) < 1e-6
+    assert g.stats()["device_status"] & (2 | 16) == 0
+    g.close()
