@@ -85,6 +85,8 @@ enum { NNCA_F64 = 0, NNCA_F32 = 1 };                 /* element type of x and y 
  * coordinates relative to their cell centre and compensated accumulation
  * across source cells; bases, translations and coefficient vectors in double. */
 enum { NNCA_PREC_FP64 = 0, NNCA_PREC_FP32 = 1 };
+/* nnca_config.m2l_form */
+enum { NNCA_M2L_AUTO = 0, NNCA_M2L_FULL = 1 };
 
 typedef struct {
     int d;             /* dimension 1..4                                         */
@@ -96,7 +98,12 @@ typedef struct {
     double kparam[4];  /* [0] scale s, [1] h or a, [2] diagonal value, [3] unused */
     int symmetric;     /* must be 1: P = Q, K symmetric; uses the shortcut
                           t^{B,o} = s^{B,i}, s^{B,o} = t^{B,i} (Sec. 5)          */
-    int reserved[3];   /* set to 0                                                */
+    int m2l_form;      /* FP32 M2L of one right-hand side: NNCA_M2L_AUTO the symmetric form
+                          where it applies (every f(|p - q|) of an admissible
+                          pair evaluated once, for both u_B and u_B'; ranks up
+                          to 256), NNCA_M2L_FULL always the full form (each target sums
+                          its whole interaction list)                            */
+    int reserved[2];   /* set to 0                                                */
 } nnca_config;
 
 /* Sizes and timings of a built handle (the quantities of the paper's
@@ -129,6 +136,10 @@ typedef struct {
                                       check, 16 a bounded wait on an asynchronous
                                       copy ran out; the product's result is then
                                       not valid. 1 (ACA scratch retried) is benign. */
+    int64_t m2l_evals;             /* kernel evaluations of the FP32 M2L of one
+                                      right-hand side: m2l_pairs / 2 when it runs
+                                      in the symmetric form (each value f(|p - q|)
+                                      serves both u_B and u_B'), else m2l_pairs */
 } nnca_stats;
 
 /* Build the H^2 representation of A(i, j) = K(p_i, q_j).

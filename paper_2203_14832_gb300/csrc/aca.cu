@@ -866,11 +866,15 @@ __global__ void k_pack_sources(int64_t nc, int d, int64_t npiv, const int2 *pran
 // M2L_STAGE_CAP padded sources. Consecutive siblings (one parent Q, adjacent
 // cell ids, so adjacent packed sources) with the same mask share one record
 // and the shift c_Q - c_P. PASS 0 counts the records, PASS 1 writes them.
+// cap: padded sources per round. sym: only neighbours Q > P (admissibility and
+// the neighbour relation are symmetric, so every admissible pair of cells
+// under two different parents appears in exactly one plan; siblings are never
+// admissible, so Q = P adds nothing).
 template <int PASS>
 __global__ void k_m2l_plan(int64_t np, const int32_t *parents, int d, int num, int den, const int32_t *ccoord,
                            int64_t ncell, const int32_t *cch_beg, const int32_t *cch_end, const int32_t *nb_off,
                            const int32_t *nb_idx, const int2 *prange, const int32_t *spk_off, const double *ccen,
-                           const int64_t *rec_off, int64_t *rec_cnt, int4 *rec, float4 *rec_sh) {
+                           int cap, int sym, const int64_t *rec_off, int64_t *rec_cnt, int4 *rec, float4 *rec_sh) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
         const int P = parents[i];
         const int cb = cch_beg[P], nch = cch_end[P] - cb;
@@ -879,6 +883,7 @@ __global__ void k_m2l_plan(int64_t np, const int32_t *parents, int d, int num, i
         int used = 0, nr = 0, last_y = -2, last_mask = -1, last_q = -1;
         for (int q = nb_off[P]; q < nb_off[P + 1]; ++q) {
             const int Q = nb_idx[q];
+            if (sym && Q <= P) continue;
             for (int y = cch_beg[Q]; y < cch_end[Q]; ++y) {
                 const int rank = prange[y].y;
                 if (rank == 0) continue;
@@ -896,14 +901,14 @@ __global__ void k_m2l_plan(int64_t np, const int32_t *parents, int d, int num, i
                 }
                 if (!mask) continue;
                 const int npad = m2l_padded(rank);
-                if (nr > 0 && Q == last_q && y == last_y + 1 && mask == last_mask && used + npad <= M2L_STAGE_CAP) {
+                if (nr > 0 && Q == last_q && y == last_y + 1 && mask == last_mask && used + npad <= cap) {
                     // the next sibling with the same mask extends the last record
                     if (PASS) out[n - 1].z += (npad >> 1) << 11;
                     used += npad;
                     last_y = y;
                     continue;
                 }
-                if (nr == M2L_STAGE_RECS || used + npad > M2L_STAGE_CAP) {
+                if (nr == M2L_STAGE_RECS || used + npad > cap) {
                     if (PASS) out[first].w = nr;
                     first = n;
                     used = 0;
@@ -1244,107 +1249,203 @@ void build_finish(Handle *h) {
         }
         std::stable_sort(groups.begin(), groups.end(), [](const Group &x, const Group &y) { return x.weight > y.weight; });
         const int64_t np = (int64_t)parents.size();
-        std::vector<int64_t> roff(np + 1, 0);
-        h->n_m2l_plan = 0;
-        if (np > 0 && !h->m2l_fp32_unsupported) {
-            int32_t *dpar = scr.get<int32_t>(np);
+        int32_t *dpar = np > 0 ? scr.get<int32_t>(np) : nullptr;
+        if (np > 0) NNCA_CUDA(cudaMemcpy(dpar, parents.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice));
+        // staging plans of all parents (cap sources per round; sym: neighbours Q > P only)
+        auto build_plan = [&](int cap, int sym, int4 *&plan, float4 *&plan_sh, int64_t &nplan,
+                              std::vector<int64_t> &roff) {
+            roff.assign(np + 1, 0);
+            nplan = 0;
             int64_t *dcnt = scr.get<int64_t>(np), *doff = scr.get<int64_t>(np);
-            NNCA_CUDA(cudaMemcpy(dpar, parents.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice));
             k_m2l_plan<0><<<grid_for(np, 128), 128, 0, s>>>(np, dpar, d, h->cfg.eta2_num, h->cfg.eta2_den, h->ccoord, nc,
                                                            h->cch_beg, h->cch_end, h->nb_off, h->nb_idx, h->prange,
-                                                           h->spk_off, h->ccen, nullptr, dcnt, nullptr, nullptr);
+                                                           h->spk_off, h->ccen, cap, sym, nullptr, dcnt, nullptr, nullptr);
             NNCA_LAUNCH_CHECK();
             std::vector<int64_t> hcnt(np);
             NNCA_CUDA(cudaMemcpy(hcnt.data(), dcnt, np * sizeof(int64_t), cudaMemcpyDeviceToHost));
             for (int64_t i = 0; i < np; ++i) roff[i + 1] = roff[i] + hcnt[i];
             NNCA_REQUIRE(roff[np] < (1ll << 31), NNCA_ERR_UNSUPPORTED, "FP32 M2L plan exceeds 2^31 records");
-            h->n_m2l_plan = roff[np];
-            h->m2l_plan = dalloc<int4>(h, roff[np]);
-            h->m2l_plan_sh = dalloc<float4>(h, roff[np]);
+            nplan = roff[np];
+            plan = dalloc<int4>(h, roff[np]);
+            plan_sh = dalloc<float4>(h, roff[np]);
             NNCA_CUDA(cudaMemcpy(doff, roff.data(), np * sizeof(int64_t), cudaMemcpyHostToDevice));
             k_m2l_plan<1><<<grid_for(np, 128), 128, 0, s>>>(np, dpar, d, h->cfg.eta2_num, h->cfg.eta2_den, h->ccoord, nc,
                                                            h->cch_beg, h->cch_end, h->nb_off, h->nb_idx, h->prange,
-                                                           h->spk_off, h->ccen, doff, nullptr, h->m2l_plan,
-                                                           h->m2l_plan_sh);
+                                                           h->spk_off, h->ccen, cap, sym, doff, nullptr, plan, plan_sh);
             NNCA_LAUNCH_CHECK();
-        }
+        };
         // Items, heaviest first. An item whose pairs (targets x staged sources)
         // exceed a share of the whole that one block of a full wave would carry
         // (total / (4 * 5 * SMs)) is cut at staging-round boundaries into pieces of
         // about equal work, so that no single block holds the launch's tail.
-        std::vector<int4> hplan(h->n_m2l_plan);
-        if (h->n_m2l_plan)
-            NNCA_CUDA(cudaMemcpy(hplan.data(), h->m2l_plan, h->n_m2l_plan * sizeof(int4), cudaMemcpyDeviceToHost));
-        struct Round { int k, n; int64_t src; };
-        std::vector<std::vector<Round>> rounds(np);
-        for (int64_t i = 0; i < np && h->n_m2l_plan; ++i)
-            for (int64_t k = roff[i]; k < roff[i + 1];) {
-                const int nrec = hplan[k].w;
-                NNCA_REQUIRE(nrec >= 1 && k + nrec <= roff[i + 1], NNCA_ERR_INTERNAL, "malformed M2L staging plan");
-                int64_t src = 0;
-                for (int e = 0; e < nrec; ++e) src += 2 * ((hplan[k + e].z >> 11) & 0x7ff);
-                rounds[i].push_back({(int)k, nrec, src});
-                k += nrec;
-            }
         int dev = 0, nsm = 152;
         NNCA_CUDA(cudaGetDevice(&dev));
         NNCA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        int64_t total = 0;
-        for (auto &g : groups)
-            for (auto &r : rounds[g.parent_slot]) total += (int64_t)g.nt * r.src;
-        const int64_t wmax = std::max<int64_t>(1, total / ((int64_t)nsm * 5 * 4));
-        struct Piece { int64_t weight; int4 item; int part; };
-        std::vector<Piece> pieces;
-        std::vector<int4> splits;
-        int nparts = 0;
-        for (auto &g : groups) {
-            const int P = parents[g.parent_slot];
-            const auto &R = rounds[g.parent_slot];
-            int64_t wsum = 0;
-            for (auto &r : R) wsum += (int64_t)g.nt * r.src;
-            const int64_t want = std::min<int64_t>((int64_t)R.size(), std::max<int64_t>(1, (wsum + wmax - 1) / wmax));
-            if (want <= 1) {
-                pieces.push_back({wsum, make_int4(P, g.t0 | (g.nt << 16), (int)roff[g.parent_slot],
-                                                  (int)(roff[g.parent_slot + 1] - roff[g.parent_slot])), -1});
-                continue;
+        struct Round { int k, n; int64_t src; };
+        struct ItemSet {
+            std::vector<int4> items;
+            std::vector<int> part;
+            std::vector<int4> splits;
+            int nparts = 0;
+        };
+        auto make_items = [&](const int4 *plan, int64_t nplan, const std::vector<int64_t> &roff, bool skip_empty,
+                              std::vector<int4> &hplan, ItemSet &out) {
+            hplan.assign(nplan, make_int4(0, 0, 0, 0));
+            if (nplan) NNCA_CUDA(cudaMemcpy(hplan.data(), plan, nplan * sizeof(int4), cudaMemcpyDeviceToHost));
+            std::vector<std::vector<Round>> rounds(np);
+            for (int64_t i = 0; i < np && nplan; ++i)
+                for (int64_t k = roff[i]; k < roff[i + 1];) {
+                    const int nrec = hplan[k].w;
+                    NNCA_REQUIRE(nrec >= 1 && k + nrec <= roff[i + 1], NNCA_ERR_INTERNAL, "malformed M2L staging plan");
+                    int64_t src = 0;
+                    for (int e = 0; e < nrec; ++e) src += 2 * ((hplan[k + e].z >> 11) & 0x7ff);
+                    rounds[i].push_back({(int)k, nrec, src});
+                    k += nrec;
+                }
+            int64_t total = 0;
+            for (auto &g : groups)
+                for (auto &r : rounds[g.parent_slot]) total += (int64_t)g.nt * r.src;
+            const int64_t wmax = std::max<int64_t>(1, total / ((int64_t)nsm * 5 * 4));
+            struct Piece { int64_t weight; int4 item; int part; };
+            std::vector<Piece> pieces;
+            for (auto &g : groups) {
+                const int P = parents[g.parent_slot];
+                const auto &R = rounds[g.parent_slot];
+                if (skip_empty && R.empty()) continue;
+                int64_t wsum = 0;
+                for (auto &r : R) wsum += (int64_t)g.nt * r.src;
+                const int64_t want = std::min<int64_t>((int64_t)R.size(), std::max<int64_t>(1, (wsum + wmax - 1) / wmax));
+                if (want <= 1) {
+                    pieces.push_back({wsum, make_int4(P, g.t0 | (g.nt << 16), (int)roff[g.parent_slot],
+                                                      (int)(roff[g.parent_slot + 1] - roff[g.parent_slot])), -1});
+                    continue;
+                }
+                const int first = out.nparts;
+                int64_t acc = 0, cut = 0;
+                size_t r0 = 0;
+                for (size_t r = 0; r < R.size(); ++r) {
+                    acc += (int64_t)g.nt * R[r].src;
+                    const bool last = r + 1 == R.size();
+                    if (last || acc * want >= (cut + 1) * wsum) {
+                        const int k0 = R[r0].k, k1 = R[r].k + R[r].n;
+                        int64_t wp = 0;
+                        for (size_t q = r0; q <= r; ++q) wp += (int64_t)g.nt * R[q].src;
+                        pieces.push_back({wp, make_int4(P, g.t0 | (g.nt << 16), k0, k1 - k0), out.nparts++});
+                        r0 = r + 1;
+                        ++cut;
+                    }
+                }
+                out.splits.push_back(make_int4((int)(hpo[hchb[P]] + g.t0), g.nt, first, out.nparts - first));
             }
-            const int first = nparts;
-            int64_t acc = 0, cut = 0;
-            size_t r0 = 0;
-            for (size_t r = 0; r < R.size(); ++r) {
-                acc += (int64_t)g.nt * R[r].src;
-                const bool last = r + 1 == R.size();
-                if (last || acc * want >= (cut + 1) * wsum) {
-                    const int k0 = R[r0].k, k1 = R[r].k + R[r].n;
-                    int64_t wp = 0;
-                    for (size_t q = r0; q <= r; ++q) wp += (int64_t)g.nt * R[q].src;
-                    pieces.push_back({wp, make_int4(P, g.t0 | (g.nt << 16), k0, k1 - k0), nparts++});
-                    r0 = r + 1;
-                    ++cut;
+            std::stable_sort(pieces.begin(), pieces.end(),
+                             [](const Piece &x, const Piece &y) { return x.weight > y.weight; });
+            for (auto &p : pieces) {
+                out.items.push_back(p.item);
+                out.part.push_back(p.part);
+            }
+        };
+        std::vector<int64_t> roff;
+        std::vector<int4> hplan;
+        ItemSet full;
+        h->n_m2l_plan = 0;
+        if (np > 0 && !h->m2l_fp32_unsupported) {
+            build_plan(M2L_STAGE_CAP, 0, h->m2l_plan, h->m2l_plan_sh, h->n_m2l_plan, roff);
+            make_items(h->m2l_plan, h->n_m2l_plan, roff, false, hplan, full);
+        }
+        h->n_m2l_groups = (int)full.items.size();
+        h->m2l_groups = dalloc<int4>(h, full.items.size());
+        h->m2l_item_part = dalloc<int>(h, full.part.size());
+        h->m2l_next = dalloc<int>(h, 1);
+        if (!full.items.empty()) {
+            NNCA_CUDA(cudaMemcpy(h->m2l_groups, full.items.data(), full.items.size() * sizeof(int4),
+                                 cudaMemcpyHostToDevice));
+            NNCA_CUDA(cudaMemcpy(h->m2l_item_part, full.part.data(), full.part.size() * sizeof(int),
+                                 cudaMemcpyHostToDevice));
+        }
+        h->n_m2l_split = (int)full.splits.size();
+        h->m2l_split = dalloc<int4>(h, full.splits.size());
+        h->m2l_parts = dalloc<double>(h, (size_t)std::max(full.nparts, 1) * M2L_GROUP_TARGETS * M2L_RHS);
+        if (!full.splits.empty())
+            NNCA_CUDA(cudaMemcpy(h->m2l_split, full.splits.data(), full.splits.size() * sizeof(int4),
+                                 cudaMemcpyHostToDevice));
+
+        // The symmetric form (one right-hand side): a plan over neighbours Q > P,
+        // the column slots of every item in staging order, and per cell the slots
+        // of its pivots' column sums, in item order.
+        int64_t maxr = 0;
+        for (int64_t c = 0; c < nc; ++c) maxr = std::max<int64_t>(maxr, hpo[c + 1] - hpo[c]);
+        h->stats.m2l_evals = h->stats.m2l_pairs;
+        if (np > 0 && !h->m2l_fp32_unsupported && maxr <= M2L_SYM_CAP && h->cfg.symmetric &&
+            h->cfg.m2l_form == NNCA_M2L_AUTO) {
+            std::vector<int64_t> sroff;
+            std::vector<int4> splan;
+            ItemSet sym;
+            build_plan(M2L_SYM_CAP, 1, h->sym_plan, h->sym_plan_sh, h->n_sym_plan, sroff);
+            make_items(h->sym_plan, h->n_sym_plan, sroff, true, splan, sym);
+            std::vector<int> icol(sym.items.size());
+            std::vector<std::vector<int32_t>> per_cell(nc);
+            int64_t ncol = 0;
+            for (size_t it = 0; it < sym.items.size(); ++it) {
+                const int4 item = sym.items[it];
+                icol[it] = (int)ncol;
+                for (int64_t k = item.z; k < (int64_t)item.z + item.w;) {
+                    const int nrec = splan[k].w;
+                    int64_t rsrc = 0;
+                    for (int e = 0; e < nrec; ++e) {
+                        const int4 r = splan[k + e];
+                        const int64_t pairs = (r.z >> 11) & 0x7ff, slot = ncol + 2 * (int64_t)(r.z & 0x7ff);
+                        // the record's cells: consecutive siblings with contiguous packed sources
+                        int64_t pq = r.y;
+                        for (int32_t y = r.x; pq < r.y + pairs; ++y) {
+                            NNCA_REQUIRE(y < nc && hso[y] == pq, NNCA_ERR_INTERNAL, "malformed symmetric M2L plan");
+                            if (hpo[y + 1] > hpo[y]) per_cell[y].push_back((int32_t)(slot + 2 * (pq - r.y)));
+                            pq = hso[y + 1];
+                        }
+                        rsrc += 2 * pairs;
+                    }
+                    ncol += rsrc;
+                    NNCA_REQUIRE(ncol < (1ll << 31), NNCA_ERR_UNSUPPORTED, "symmetric M2L exceeds 2^31 column slots");
+                    k += nrec;
                 }
             }
-            splits.push_back(make_int4((int)(hpo[hchb[P]] + g.t0), g.nt, first, nparts - first));
+            std::vector<int32_t> eoff(nc + 1, 0), ent;
+            std::vector<int2> tasks;
+            for (int64_t c = 0; c < nc; ++c) {
+                eoff[c + 1] = eoff[c] + (int32_t)per_cell[c].size();
+                ent.insert(ent.end(), per_cell[c].begin(), per_cell[c].end());
+                if (!per_cell[c].empty())
+                    for (int64_t j0 = 0; j0 < hpo[c + 1] - hpo[c]; j0 += 32) tasks.push_back(make_int2((int)c, (int)j0));
+            }
+            h->n_sym_items = (int)sym.items.size();
+            h->sym_items = dalloc<int4>(h, sym.items.size());
+            h->sym_item_part = dalloc<int>(h, sym.part.size());
+            h->sym_item_col = dalloc<int>(h, icol.size());
+            h->n_sym_split = (int)sym.splits.size();
+            h->sym_split = dalloc<int4>(h, sym.splits.size());
+            h->sym_parts = dalloc<double>(h, (size_t)std::max(sym.nparts, 1) * M2L_GROUP_TARGETS);
+            h->n_sym_col = ncol;
+            h->sym_col = dalloc<float>(h, (size_t)ncol);
+            h->sym_ent_off = dalloc<int32_t>(h, nc + 1);
+            h->sym_ent = dalloc<int32_t>(h, ent.size());
+            h->n_sym_tasks = (int)tasks.size();
+            h->sym_tasks = dalloc<int2>(h, tasks.size());
+            if (!sym.items.empty()) {
+                NNCA_CUDA(cudaMemcpy(h->sym_items, sym.items.data(), sym.items.size() * sizeof(int4),
+                                     cudaMemcpyHostToDevice));
+                NNCA_CUDA(cudaMemcpy(h->sym_item_part, sym.part.data(), sym.part.size() * sizeof(int),
+                                     cudaMemcpyHostToDevice));
+                NNCA_CUDA(cudaMemcpy(h->sym_item_col, icol.data(), icol.size() * sizeof(int), cudaMemcpyHostToDevice));
+            }
+            if (!sym.splits.empty())
+                NNCA_CUDA(cudaMemcpy(h->sym_split, sym.splits.data(), sym.splits.size() * sizeof(int4),
+                                     cudaMemcpyHostToDevice));
+            NNCA_CUDA(cudaMemcpy(h->sym_ent_off, eoff.data(), (nc + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+            if (!ent.empty())
+                NNCA_CUDA(cudaMemcpy(h->sym_ent, ent.data(), ent.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+            if (!tasks.empty())
+                NNCA_CUDA(cudaMemcpy(h->sym_tasks, tasks.data(), tasks.size() * sizeof(int2), cudaMemcpyHostToDevice));
+            h->stats.m2l_evals = h->stats.m2l_pairs / 2;
         }
-        std::stable_sort(pieces.begin(), pieces.end(), [](const Piece &x, const Piece &y) { return x.weight > y.weight; });
-        std::vector<int4> v;
-        std::vector<int> vp;
-        for (auto &p : pieces) {
-            v.push_back(p.item);
-            vp.push_back(p.part);
-        }
-        h->n_m2l_groups = (int)v.size();
-        h->m2l_groups = dalloc<int4>(h, v.size());
-        h->m2l_item_part = dalloc<int>(h, vp.size());
-        h->m2l_next = dalloc<int>(h, 1);
-        if (!v.empty()) {
-            NNCA_CUDA(cudaMemcpy(h->m2l_groups, v.data(), v.size() * sizeof(int4), cudaMemcpyHostToDevice));
-            NNCA_CUDA(cudaMemcpy(h->m2l_item_part, vp.data(), vp.size() * sizeof(int), cudaMemcpyHostToDevice));
-        }
-        h->n_m2l_split = (int)splits.size();
-        h->m2l_split = dalloc<int4>(h, splits.size());
-        h->m2l_parts = dalloc<double>(h, (size_t)std::max(nparts, 1) * M2L_GROUP_TARGETS * M2L_RHS);
-        if (!splits.empty())
-            NNCA_CUDA(cudaMemcpy(h->m2l_split, splits.data(), splits.size() * sizeof(int4), cudaMemcpyHostToDevice));
         NNCA_CUDA(cudaStreamSynchronize(s));
     }
     {

@@ -155,6 +155,8 @@ nnca_status nnca_build(const nnca_config *cfg, const double *P, int64_t nP, cons
         return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_build: unknown layout");
     if (cfg->symmetric != 1)
         return fail(nullptr, NNCA_ERR_UNSUPPORTED, "nnca_build: only the symmetric form (P = Q, symmetric K) is built");
+    if (cfg->m2l_form != NNCA_M2L_AUTO && cfg->m2l_form != NNCA_M2L_FULL)
+        return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_build: unknown m2l_form");
     if (Q && (Q != P || nQ != nP))
         return fail(nullptr, NNCA_ERR_UNSUPPORTED, "nnca_build: P != Q is not supported (pass Q = NULL or Q = P)");
     if (!is_device_ptr(P)) return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_build: P is not device memory");

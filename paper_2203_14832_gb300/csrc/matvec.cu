@@ -592,6 +592,36 @@ struct M2lGroupSmem {
     int abort;
 };
 
+// The symmetric form's block state: the same staging buffers (rounds of at most
+// M2L_SYM_CAP sources), each warp's column sums of the rounds in flight, a
+// per-warp transpose buffer for the column sums of one chunk, and per buffer
+// the round's first column slot, its sources and the warps done with it.
+constexpr int M2L_SYM_COLBUF = 32 * (2 * M2L_FOLD + 1);   // float2 per warp: L rows of 2 M2L_FOLD G + 1, L G <= 32
+struct M2lSymSmem {
+    float4 src[M2L_STAGE_BUFS][M2L_SYM_CAP / 2][2];
+    float colw[M2L_STAGE_BUFS][M2L_GROUP_WARPS][M2L_SYM_CAP];
+    float2 colbuf[M2L_GROUP_WARPS][M2L_SYM_COLBUF];
+    int hdr[M2L_STAGE_BUFS][M2L_STAGE_RECS];
+    float4 sh[M2L_STAGE_BUFS][M2L_STAGE_RECS];
+    int nrec[M2L_STAGE_BUFS], rbase[M2L_STAGE_BUFS], rsrc[M2L_STAGE_BUFS], cnt[M2L_STAGE_BUFS];
+    unsigned long long full[M2L_STAGE_BUFS], empty[M2L_STAGE_BUFS];
+    int2 ch_range[8];
+    int item;
+    int abort;
+    int scol;   // next column slot of the item (staging warp)
+};
+
+// what the staging warp records about a round besides its records
+__device__ __forceinline__ void stage_note(M2lGroupSmem &, int, unsigned) {}
+__device__ __forceinline__ void stage_note(M2lSymSmem &S, int b, unsigned bytes) {
+    if ((threadIdx.x & 31) == 0) {
+        const int n = (int)(bytes / 16u);   // 32 bytes per source pair
+        S.rbase[b] = S.scol;
+        S.rsrc[b] = n;
+        S.scol += n;
+    }
+}
+
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(void *bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
@@ -650,7 +680,8 @@ __device__ __forceinline__ void stage_load(StageCursor &c, const int4 *plan, con
 // (after the warps have released its previous use), then load the records of
 // the round after it. Returns the first record of that round, or kend after a
 // timed-out wait or a malformed record.
-__device__ __forceinline__ int m2l_stage(M2lGroupSmem &S, int b, unsigned use, StageCursor &cur, const int4 *plan,
+template <class SM>
+__device__ __forceinline__ int m2l_stage(SM &S, int b, unsigned use, StageCursor &cur, const int4 *plan,
                                          const float4 *plan_sh, int kend, const float4 *spk, unsigned *status) {
     const int lane = threadIdx.x & 31;
     if (use > 0 && !mbar_wait_warp(&S.empty[b], (use - 1) & 1)) {
@@ -671,6 +702,16 @@ __device__ __forceinline__ int m2l_stage(M2lGroupSmem &S, int b, unsigned use, S
     }
     unsigned bytes = 0;
     const int4 r = cur.r;
+    // every record's slots must lie inside the buffer
+    constexpr int cap_pairs = (int)(sizeof(S.src[0]) / (2 * sizeof(float4)));
+    const bool bad = lane < nrec && (r.z & 0x7ff) + ((r.z >> 11) & 0x7ff) > cap_pairs;
+    if (__any_sync(0xffffffffu, bad)) {
+        if (lane == 0) {
+            atomicOr(status, DEV_BAD_INDEX);
+            *(volatile int *)&S.abort = 1;
+        }
+        return kend;
+    }
     if (lane < nrec) {
         S.hdr[b][lane] = r.z;
         S.sh[b][lane] = cur.sh;
@@ -678,6 +719,7 @@ __device__ __forceinline__ int m2l_stage(M2lGroupSmem &S, int b, unsigned use, S
     }
     const unsigned total = __reduce_add_sync(0xffffffffu, bytes);
     if (lane == 0) S.nrec[b] = nrec;
+    stage_note(S, b, total);
     __syncwarp();
     if (lane == 0) mbar_arrive_tx(&S.full[b], total);
     __syncwarp();
@@ -1619,6 +1661,254 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group_rhs(KParams kp,
         for (unsigned r = R; r < Rp; ++r) mbar_wait(&S.full[r % M2L_STAGE_BUFS], (r / M2L_STAGE_BUFS) & 1);
 }
 
+// ---- M2L, FP32, symmetric form (one right-hand side) ------------------------------
+// f(|s - t|) = f(|t - s|), and Y is in IL(X) exactly when X is in IL(Y)
+// (admissibility and the neighbour relation are symmetric). So the plan of
+// parent P lists only the children of its neighbours Q > P, and every kernel
+// value a block evaluates serves twice: in the row sum u_X(t) += f w_Y(s), as in
+// k_m2l_group, and in the column sum u_Y(s) += f w_X(t). Column sums of one
+// chunk of sources (M2L_FOLD couples of pairs per lane) go through a per-warp
+// transpose buffer and are summed over the warp's targets in a fixed order;
+// the last warp to finish a round adds the four warps' sums (warp order) and
+// writes them to the item's column slots; k_m2l_cols adds each cell's slots
+// into u in a fixed order. The result is deterministic.
+
+// the source pairs q0, q0 + step, ... below q1 (two at a time) of one staged
+// segment against two targets: row sums into a*, b*; the column values
+// f_a w_a + f_b w_b of each source pair into crow[q]
+template <int KIND, int FULL>
+__device__ __forceinline__ void m2l_sym_pairs(const KParams &kp, const float4 (*src)[2], int q0, int q1, f2 xa, f2 ya,
+                                              f2 za, f2 xb, f2 yb, f2 zb, f2 WA, f2 WB, f2 *crow, f2 &a0, f2 &a1,
+                                              f2 &b0, f2 &b1, int step = 2) {
+    if (FULL) step = 2;
+    for (int q = q0; q < q1; q += step) {
+        const ulonglong2 A0 = *reinterpret_cast<const ulonglong2 *>(&src[q][0]);
+        const ulonglong2 B0 = *reinterpret_cast<const ulonglong2 *>(&src[q][1]);
+        const ulonglong2 A1 = *reinterpret_cast<const ulonglong2 *>(&src[q + 1][0]);
+        const ulonglong2 B1 = *reinterpret_cast<const ulonglong2 *>(&src[q + 1][1]);
+        const f2 fa0 = group_f<KIND>(kp, A0, B0, xa, ya, za), fb0 = group_f<KIND>(kp, A0, B0, xb, yb, zb);
+        const f2 fa1 = group_f<KIND>(kp, A1, B1, xa, ya, za), fb1 = group_f<KIND>(kp, A1, B1, xb, yb, zb);
+        a0 = f2_fma(fa0, B0.y, a0);
+        b0 = f2_fma(fb0, B0.y, b0);
+        a1 = f2_fma(fa1, B1.y, a1);
+        b1 = f2_fma(fb1, B1.y, b1);
+        crow[q] = f2_fma(fb0, WB, f2_mul(fa0, WA));
+        crow[q + 1] = f2_fma(fb1, WB, f2_mul(fa1, WA));
+    }
+}
+
+// Column sums of one chunk: the transpose buffer holds, per target lane t < L
+// (row t, stride rs), the column values of the chunk's np2 source pairs. Lane
+// (h, p) sums pair p over one half of the rows, in row order; the halves are
+// added (half 0 + half 1) and written as the pair's two column sums.
+__device__ __forceinline__ void m2l_sym_columns(const f2 *cbuf, int rs, int L, int G, int np2, int lane, f2 *out) {
+    const int h = lane >> 4, pl = lane & 15;
+    for (int pb = 0; pb < np2; pb += 16) {
+        const int p = pb + pl;
+        f2 s0 = 0ull, s1 = 0ull;
+        if (p < np2) {
+            if (G == 1 && L == 32) {   // full warp: rows 16 h .. 16 h + 15, stride 2 M2L_FOLD + 1
+                const f2 *c = cbuf + 16 * h * (2 * M2L_FOLD + 1) + p;
+#pragma unroll
+                for (int k = 0; k < 16; k += 2) {
+                    s0 = f2_add(s0, c[k * (2 * M2L_FOLD + 1)]);
+                    s1 = f2_add(s1, c[(k + 1) * (2 * M2L_FOLD + 1)]);
+                }
+            } else {
+                const int hl = (L + 1) >> 1, r0 = h ? hl : 0, r1 = h ? L : hl;
+                for (int r = r0; r < r1; ++r) s0 = f2_add(s0, cbuf[r * rs + p]);
+            }
+        }
+        const f2 mine = f2_add(s0, s1);
+        const f2 other = __shfl_xor_sync(0xffffffffu, mine, 16);
+        if (h == 0 && p < np2) out[p] = f2_add(mine, other);
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_sym(KParams kp, const int4 *items, int nitems,
+                                                             int *next_item, const int4 *plan, const float4 *plan_sh,
+                                                             const int32_t *cch_beg, const int32_t *cch_end,
+                                                             const int2 *prange, const float4 *pv4, const float4 *chi,
+                                                             const float4 *clo, const float4 *spk, const double *w,
+                                                             const int *item_part, const int *item_col, double *parts,
+                                                             double *u, float *col, unsigned *status) {
+    extern __shared__ __align__(128) unsigned char sym_smem[];
+    M2lSymSmem &S = *reinterpret_cast<M2lSymSmem *>(sym_smem);
+    const int tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
+    if (tid == 0) {
+        for (int b = 0; b < M2L_STAGE_BUFS; ++b) {
+            mbar_init(&S.full[b], 1);
+            mbar_init(&S.empty[b], M2L_GROUP_WARPS);
+            S.cnt[b] = 0;
+        }
+        S.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const int pw = blockIdx.x % M2L_GROUP_WARPS;
+    unsigned R = 0, Rp = 0;
+    f2 *cbuf = reinterpret_cast<f2 *>(S.colbuf[wl]);
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) S.item = atomicAdd(next_item, 1);
+        __syncthreads();
+        const int it = S.item;
+        if (it >= nitems || *(volatile int *)&S.abort) break;
+        const int4 item = items[it];
+        const int part = item_part[it];
+        const int P = item.x, t0 = item.y & 0xffff, nt = item.y >> 16, kend = item.z + item.w;
+        const int cb = cch_beg[P], nch = cch_end[P] - cb;
+        if (tid < nch) S.ch_range[tid] = prange[cb + tid];
+        if (tid == 0) S.scol = item_col[it];
+        __syncthreads();
+        const float4 hP = chi[P], lP = clo[P];
+        int kprod = item.z, kcons = item.z;
+        StageCursor cur;
+        if (wl == pw && kprod < kend) stage_load(cur, plan, plan_sh, kprod, kend);
+        const int wj0 = t0 + wl * M2L_WARP_TARGETS, jend = t0 + nt;
+        const int cw = min(M2L_WARP_TARGETS, max(0, jend - wj0));
+        const int L = cw > 0 ? (cw + 1) / 2 : 32;
+        const int G = min(16, 32 / L);
+        const int grp = lane / L, ti = lane - grp * L;
+        const bool live = grp < G;
+        const int j = wj0 + 2 * ti;
+        const int g = S.ch_range[0].x + j;
+        GroupTarget Ta, Tb;
+        group_target(Ta, live && j < jend, g, nch, cb, S.ch_range, pv4, chi, clo, hP, lP);
+        group_target(Tb, live && j + 1 < jend, g + 1, nch, cb, S.ch_range, pv4, chi, clo, hP, lP);
+        const float wa = Ta.c < 31 ? (float)w[Ta.g] : 0.f, wb = Tb.c < 31 ? (float)w[Tb.g] : 0.f;
+        const unsigned omask =
+            __reduce_or_sync(0xffffffffu, (Ta.c < 31 ? 1u << Ta.c : 0u) | (Tb.c < 31 ? 1u << Tb.c : 0u));
+        const int span = 2 * M2L_FOLD * G, rs = span + 1;   // chunk (source pairs) and transpose row length
+        while (kcons < kend) {
+            if (wl == pw)
+                while (kprod < kend && Rp <= R + M2L_STAGE_AHEAD) {
+                    kprod = m2l_stage(S, Rp % M2L_STAGE_BUFS, Rp / M2L_STAGE_BUFS, cur, plan, plan_sh, kend, spk,
+                                      status);
+                    ++Rp;
+                }
+            const int b = R % M2L_STAGE_BUFS;
+            if (!mbar_wait_warp(&S.full[b], (R / M2L_STAGE_BUFS) & 1)) {
+                if (lane == 0) {
+                    atomicOr(status, DEV_WAIT_TIMEOUT);
+                    *(volatile int *)&S.abort = 1;
+                }
+                break;
+            }
+            const int nrec = S.nrec[b];
+            if (nrec < 1) break;   // unreachable with a well-formed plan
+            float *cwb = S.colw[b][wl];
+            for (int i = 0; i < nrec; ++i) {
+                const int hw = S.hdr[b][i];
+                const unsigned m = ((unsigned)hw >> 22) & omask;
+                const int q0 = hw & 0x7ff, q1 = q0 + ((hw >> 11) & 0x7ff);
+                if (!m) {   // no target of this warp sees the segment: its column sums here are 0
+                    for (int e = 2 * q0 + lane; e < 2 * q1; e += 32) cwb[e] = 0.f;
+                    continue;
+                }
+                const float4 sh = S.sh[b][i];
+                const f2 SX = f2_pack(sh.x, sh.x), SY = f2_pack(sh.y, sh.y), SZ = f2_pack(sh.z, sh.z);
+                const f2 xa = f2_sub(Ta.tx, SX), ya = f2_sub(Ta.ty, SY), za = f2_sub(Ta.tz, SZ);
+                const f2 xb = f2_sub(Tb.tx, SX), yb = f2_sub(Tb.ty, SY), zb = f2_sub(Tb.tz, SZ);
+                const bool ona = (m >> Ta.c) & 1u, onb = (m >> Tb.c) & 1u;
+                const float ea = ona ? wa : 0.f, eb = onb ? wb : 0.f;
+                const f2 WA = f2_pack(ea, ea), WB = f2_pack(eb, eb);
+                for (int c0 = q0; c0 < q1; c0 += span) {
+                    const int c1 = min(q1, c0 + span);
+                    if (live) {
+                        f2 a0 = 0ull, a1 = 0ull, b0 = 0ull, b1 = 0ull;
+                        f2 *crow = cbuf + ti * rs - c0;
+                        if (G == 1)
+                            m2l_sym_pairs<KIND, 1>(kp, S.src[b], c0, c1, xa, ya, za, xb, yb, zb, WA, WB, crow, a0, a1, b0,
+                                                   b1);
+                        else
+                            m2l_sym_pairs<KIND, 0>(kp, S.src[b], c0 + 2 * grp, c1, xa, ya, za, xb, yb, zb, WA, WB, crow,
+                                                   a0, a1, b0, b1, 2 * G);
+                        const float2 pa = f2_unpack(f2_add(a0, a1)), pb = f2_unpack(f2_add(b0, b1));
+                        if (ona) two_sum_add(Ta.sum, Ta.comp, pa.x + pa.y);
+                        if (onb) two_sum_add(Tb.sum, Tb.comp, pb.x + pb.y);
+                    }
+                    __syncwarp();
+                    m2l_sym_columns(cbuf, rs, L, G, c1 - c0, lane, reinterpret_cast<f2 *>(cwb) + c0);
+                    __syncwarp();
+                }
+            }
+            // this warp's column sums of the round are in colw[b][wl]; the last
+            // warp to get here adds the four in warp order and writes the slots
+            __threadfence_block();
+            __syncwarp();
+            int last = 0;
+            if (lane == 0) last = atomicAdd(&S.cnt[b], 1) == M2L_GROUP_WARPS - 1;
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence_block();
+                const int ns = min(S.rsrc[b], M2L_SYM_CAP);
+                float *dst = col + S.rbase[b];
+                for (int e = lane; e < ns; e += 32)
+                    dst[e] = (S.colw[b][0][e] + S.colw[b][1][e]) + (S.colw[b][2][e] + S.colw[b][3][e]);
+                __syncwarp();
+                if (lane == 0) S.cnt[b] = 0;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.empty[b]);
+            ++R;
+            kcons += nrec;
+        }
+        for (int gg = 1; gg < G; ++gg) {
+            const int srcl = min(ti + gg * L, 31);
+            const float sa = __shfl_sync(0xffffffffu, Ta.sum, srcl), ca = __shfl_sync(0xffffffffu, Ta.comp, srcl);
+            const float sb = __shfl_sync(0xffffffffu, Tb.sum, srcl), cb2 = __shfl_sync(0xffffffffu, Tb.comp, srcl);
+            if (grp == 0) {
+                two_sum_add(Ta.sum, Ta.comp, sa);
+                Ta.comp += ca;
+                two_sum_add(Tb.sum, Tb.comp, sb);
+                Tb.comp += cb2;
+            }
+        }
+        if (grp == 0) {
+            const int gb = S.ch_range[0].x + t0;
+            double *dst = part < 0 ? u + gb : parts + (int64_t)part * M2L_GROUP_TARGETS;
+            if (Ta.c < 31) dst[Ta.g - gb] = kp.s * ((double)Ta.sum + (double)Ta.comp);
+            if (Tb.c < 31) dst[Tb.g - gb] = kp.s * ((double)Tb.sum + (double)Tb.comp);
+        }
+    }
+    if (wl == pw && lane == 0)
+        for (unsigned r = R; r < Rp; ++r) mbar_wait(&S.full[r % M2L_STAGE_BUFS], (r / M2L_STAGE_BUFS) & 1);
+}
+
+// column sums of the symmetric M2L: u(Y) += s * (Y's slots, in their fixed order).
+// One warp per task (cell Y, first pivot j0): lane j0 + l sums its column over
+// Y's slots, reading 32 slot offsets at a time and issuing the 32 slot loads
+// before adding them; the sums are compensated float sums (two-sum), so no
+// FP64 arithmetic sits in the loop
+__global__ void k_m2l_cols(const int2 *tasks, int ntasks, const int32_t *ent_off, const int32_t *ent,
+                           const int2 *prange, const float *col, double s, double *u) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    for (int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5); i < ntasks; i += nw) {
+        const int2 tk = tasks[i];
+        const int Y = tk.x;
+        const int2 pr = prange[Y];
+        const int e0 = ent_off[Y], e1 = ent_off[Y + 1];
+        const int jj = tk.y + lane;
+        const bool on = jj < pr.y;
+        float sum = 0.f, comp = 0.f;
+        for (int eb = e0; eb < e1; eb += 32) {
+            const int n = min(32, e1 - eb);
+            const int my = lane < n ? ent[eb + lane] : 0;
+            float f[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int sl = __shfl_sync(0xffffffffu, my, q);
+                f[q] = on && q < n ? col[sl + jj] : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < 32; ++q) two_sum_add(sum, comp, f[q]);   // a 0 leaves (sum, comp) unchanged
+        }
+        if (on) u[pr.x + jj] += s * ((double)sum + (double)comp);
+    }
+}
+
 // u of the targets of a split item: the sum of its pieces' partial sums, in piece order
 // (nr right-hand sides: slot s holds nr consecutive rows of M2L_GROUP_TARGETS)
 __global__ void k_m2l_combine(const int4 *split, int nsplit, const double *parts, double *u, int nr, int64_t npiv) {
@@ -1651,6 +1941,40 @@ void launch_m2l_f32(Handle *h, double *u) {
     if (h->n_m2l_split) {
         k_m2l_combine<<<(unsigned)std::min(h->n_m2l_split, 152 * 16), 256, 0, h->stream>>>(h->m2l_split, h->n_m2l_split,
                                                                                           h->m2l_parts, u, 1, h->npiv);
+        NNCA_LAUNCH_CHECK();
+        ++h->launches;
+    }
+}
+
+// the symmetric form: rows by k_m2l_sym (and the split pieces' combine), then
+// the column sums of every cell
+template <int KIND>
+void launch_m2l_sym(Handle *h, const double *w, double *u) {
+    const int smem = (int)sizeof(M2lSymSmem);
+    NNCA_CUDA(cudaFuncSetAttribute(k_m2l_sym<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int dev = 0, nsm = 152, per_sm = 1;
+    NNCA_CUDA(cudaGetDevice(&dev));
+    NNCA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (h->n_sym_items) {
+        NNCA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_m2l_sym<KIND>, M2L_GROUP_THREADS, smem));
+        const unsigned g = (unsigned)std::min<int64_t>(h->n_sym_items, (int64_t)nsm * std::max(1, per_sm));
+        NNCA_CUDA(cudaMemsetAsync(h->m2l_next, 0, sizeof(int), h->stream));
+        k_m2l_sym<KIND><<<g, M2L_GROUP_THREADS, smem, h->stream>>>(
+            h->kp, h->sym_items, h->n_sym_items, h->m2l_next, h->sym_plan, h->sym_plan_sh, h->cch_beg, h->cch_end,
+            h->prange, h->pv4, h->chi4, h->clo4, h->spk, w, h->sym_item_part, h->sym_item_col, h->sym_parts, u,
+            h->sym_col, h->dev_status);
+        NNCA_LAUNCH_CHECK();
+        ++h->launches;
+    }
+    if (h->n_sym_split) {
+        k_m2l_combine<<<(unsigned)std::min(h->n_sym_split, 152 * 16), 256, 0, h->stream>>>(h->sym_split, h->n_sym_split,
+                                                                                          h->sym_parts, u, 1, h->npiv);
+        NNCA_LAUNCH_CHECK();
+        ++h->launches;
+    }
+    if (h->n_sym_tasks) {
+        k_m2l_cols<<<grid_for((int64_t)h->n_sym_tasks * 32, 256), 256, 0, h->stream>>>(
+            h->sym_tasks, h->n_sym_tasks, h->sym_ent_off, h->sym_ent, h->prange, h->sym_col, h->kp.s, u);
         NNCA_LAUNCH_CHECK();
         ++h->launches;
     }
@@ -1792,6 +2116,8 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
             if (!kernel_is_radial(h->kp.kind)) {
                 k_m2l_generic<NR><<<grid_for(h->n_m2l_tgt * 32, 128), 128, 0, s>>>(
                     h->kp, h->d, h->m2l_tgt, h->n_m2l_tgt, h->il_off, h->il_idx, h->piv_off, h->pv64, npiv, w, u);
+            } else if (FP32 && NR == 1 && h->sym_items) {
+                launch_m2l_sym<KIND>(h, w, u);
             } else if (FP32 && NR == 1) {
                 launch_m2l_f32<KIND>(h, u);
             } else if (FP32 && NR == M2L_RHS) {

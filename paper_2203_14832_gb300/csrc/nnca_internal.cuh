@@ -174,6 +174,12 @@ constexpr int M2L_STAGE_BUFS = 4;
 // right-hand sides of one FP32 M2L pass with several (their weights travel as
 // [w(2q, r) w(2q+1, r) w(2q, r+1) w(2q+1, r+1)] float4 pairs per source pair q)
 constexpr int M2L_RHS = 4;
+// The symmetric FP32 M2L (one right-hand side) serves each unordered pair of
+// neighbouring parents {P, Q} once: a kernel value f(|s - t|) feeds the row sum
+// of target t and the column sum of source s. Its rounds hold at most
+// M2L_SYM_CAP padded sources (so the per-warp column sums of the rounds in
+// flight fit in shared memory beside the staged sources).
+constexpr int M2L_SYM_CAP = 256;
 // The FP32 near field runs independent warps, NEAR_WARPS per block, one leaf
 // (up to 64 targets) per work item. The points of N(B) arrive in rounds of at
 // most NEAR_RECS cells and NEAR_CAP point pairs through NEAR_BUFS buffers per
@@ -303,6 +309,29 @@ struct Handle {
     int32_t *spk_off = nullptr;   // [ncell + 1]
     float4 *spw = nullptr;        // [pairs][M2L_RHS / 2]: weights of a pass with M2L_RHS right-hand sides
     int64_t n_spk_pairs = 0;
+    // Symmetric FP32 M2L (null sym_items: not available, the full form runs):
+    // the plan of parent P lists only the children of neighbours Q > P (cell
+    // index), in rounds of at most M2L_SYM_CAP sources; items and split pieces as
+    // for the full form. Item i writes the column sums of its staged sources, in
+    // staging order, to sym_col[sym_item_col[i] ...]; cell Y gathers its column
+    // sums from the slots sym_ent[sym_ent_off[Y] .. sym_ent_off[Y + 1]) (each the
+    // slot of Y's first pivot) in that fixed order.
+    int4 *sym_plan = nullptr;
+    float4 *sym_plan_sh = nullptr;
+    int64_t n_sym_plan = 0;
+    int4 *sym_items = nullptr;
+    int n_sym_items = 0;
+    int *sym_item_part = nullptr;
+    int *sym_item_col = nullptr;
+    double *sym_parts = nullptr;
+    int4 *sym_split = nullptr;
+    int n_sym_split = 0;
+    float *sym_col = nullptr;
+    int64_t n_sym_col = 0;
+    int32_t *sym_ent_off = nullptr;   // [ncell + 1]
+    int32_t *sym_ent = nullptr;
+    int2 *sym_tasks = nullptr;        // (cell with slots, first of 32 pivots) per warp of the column pass
+    int n_sym_tasks = 0;
     int2 *leaf_items[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int n_leaf_items[5] = {0, 0, 0, 0, 0};
 

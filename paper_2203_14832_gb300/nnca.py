@@ -24,6 +24,7 @@ NNCA_OK, NNCA_ERR_INVALID_ARG, NNCA_ERR_OOM, NNCA_ERR_CUDA, NNCA_ERR_UNSUPPORTED
     NNCA_ERR_INTERNAL = range(7)
 K_LOG, K_INV_R, K_GAUSS, K_MATERN, K_PAPER_I, K_PAPER_II, K_SEPARABLE, K_POLY2 = range(8)
 LAYOUT_AOS, LAYOUT_SOA = 0, 1
+M2L_AUTO, M2L_FULL = 0, 1
 F64, F32 = 0, 1
 PREC_FP64, PREC_FP32 = 0, 1
 EXPORTS = ["PERM", "KEYS", "LEVEL_BASE", "CKEY", "CBEG", "CEND", "CPAR", "CCH_BEG", "CCH_END", "NB_OFF", "NB_IDX",
@@ -41,7 +42,7 @@ class NncaError(RuntimeError):
 class _Config(C.Structure):
     _fields_ = [("d", C.c_int), ("leaf_size", C.c_int), ("eta2_num", C.c_int), ("eta2_den", C.c_int),
                 ("aca_tol", C.c_double), ("kernel", C.c_int), ("kparam", C.c_double * 4), ("symmetric", C.c_int),
-                ("reserved", C.c_int * 3)]
+                ("m2l_form", C.c_int), ("reserved", C.c_int * 2)]
 
 
 class _Stats(C.Structure):
@@ -51,7 +52,7 @@ class _Stats(C.Structure):
                 ("p2p_pairs", C.c_int64), ("m2l_pairs", C.c_int64), ("op_entries", C.c_int64),
                 ("device_bytes", C.c_int64), ("build_ms", C.c_double * 8), ("aca_retries", C.c_int64),
                 ("pass_ms", C.c_double * 8), ("pass_calls", C.c_int64), ("launches_per_product", C.c_int64),
-                ("device_status", C.c_int64)]
+                ("device_status", C.c_int64), ("m2l_evals", C.c_int64)]
 
 
 _lib = None
@@ -102,11 +103,12 @@ class Config:
     aca_tol: float = 1e-6
     kernel: int = K_INV_R
     kparam: tuple = (1.0, 0.0, 0.0, 0.0)
+    m2l_form: int = M2L_AUTO
 
     def c(self) -> _Config:
         k = (C.c_double * 4)(*[float(v) for v in (list(self.kparam) + [0.0] * 4)[:4]])
         return _Config(self.d, self.leaf_size, self.eta2_num, self.eta2_den, float(self.aca_tol), self.kernel, k, 1,
-                       (C.c_int * 3)(0, 0, 0))
+                       self.m2l_form, (C.c_int * 2)(0, 0))
 
 
 def _check(status: int, handle=None):

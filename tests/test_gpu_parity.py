@@ -94,7 +94,41 @@ def test_full_parity(gpu, orc, wl, n, kw, tol32):
     st = g.stats()
     assert st["kappa"] == o.kappa and st["lmin"] == o.lmin and st["ncell"] == o.ncell
     assert st["device_status"] & (2 | 16) == 0   # no failed bounds check, no timed-out wait
+    # the symmetric M2L (ranks up to 256) evaluates each pivot pair once
+    assert st["m2l_evals"] == (st["m2l_pairs"] // 2 if st["max_rank"] <= 256 else st["m2l_pairs"])
     g.close()
+
+
+@pytest.mark.parametrize("wl,n,kw", [("invr3d_1m", 12000, {"leaf_size": 32}), ("sphere_512k", 12000, {}),
+                                     ("gauss_mix_256k", 12000, {"leaf_size": 32})])
+def test_m2l_forms(gpu, orc, wl, n, kw):
+    """FP32 M2L in the symmetric form (each pivot pair evaluated once, its value added to
+    the row sum of one cell and the column sum of the other) and in the full form: both
+    within 1e-6 of the oracle's FP64 product, within 1e-6 of each other, and each
+    deterministic (two products bit-identical)."""
+    import torch
+    w = W.WORKLOADS[wl].scaled(n)
+    P = w.make_points()
+    gcfg, ocfg = configs(gpu, orc, w, **kw)
+    o = orc.H2(P, ocfg)
+    x = w.make_vector() if w.nrhs == 1 else w.make_vector()[0].copy()
+    yo = o.matvec(x)
+    xd = torch.as_tensor(np.ascontiguousarray(x), device="cuda")
+    ys = {}
+    for form in (gpu.M2L_AUTO, gpu.M2L_FULL):
+        gcfg.m2l_form = form
+        g = gpu.H2(torch.as_tensor(P, device="cuda"), gcfg)
+        st = g.stats()
+        assert st["max_rank"] <= 256
+        assert st["m2l_evals"] == (st["m2l_pairs"] // 2 if form == gpu.M2L_AUTO else st["m2l_pairs"])
+        y1 = g.matvec(xd, gpu.PREC_FP32).cpu().numpy()
+        y2 = g.matvec(xd, gpu.PREC_FP32).cpu().numpy()
+        assert np.array_equal(y1, y2)
+        assert rel(y1, yo) < 1e-6
+        assert g.stats()["device_status"] & (2 | 16) == 0
+        ys[form] = y1
+        g.close()
+    assert rel(ys[gpu.M2L_AUTO], ys[gpu.M2L_FULL]) < 1e-6
 
 
 def test_dense_bound_log2d(gpu, orc):

@@ -51,3 +51,20 @@ def test_calls_without_a_device_fail_cleanly(libnnca):
     assert libnnca.nnca_status_string(1) == b"invalid argument"
     libnnca.nnca_last_error.restype = ctypes.c_char_p
     assert b"NULL" in libnnca.nnca_last_error(None)
+
+
+def test_unknown_m2l_form_is_rejected_on_the_host(libnnca):
+    """nnca_config.m2l_form takes NNCA_M2L_AUTO or NNCA_M2L_FULL; anything else fails
+    before any device call."""
+    from paper_2203_14832_gb300 import nnca
+    libnnca.nnca_build.restype = ctypes.c_int
+    libnnca.nnca_last_error.restype = ctypes.c_char_p
+    for form, ok in ((nnca.M2L_AUTO, True), (nnca.M2L_FULL, True), (2, False), (-1, False)):
+        cfg = nnca.Config(m2l_form=form).c()
+        out = ctypes.c_void_p()
+        pts = (ctypes.c_double * 30)()   # host memory: a valid form fails later, at the device check
+        st = libnnca.nnca_build(ctypes.byref(cfg), pts, ctypes.c_int64(10), None, ctypes.c_int64(0), 0, None,
+                                ctypes.byref(out))
+        assert st == 1 and not out.value
+        msg = libnnca.nnca_last_error(None)
+        assert (b"m2l_form" in msg) != ok, msg
