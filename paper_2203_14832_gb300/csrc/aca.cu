@@ -1217,8 +1217,8 @@ void build_finish(Handle *h) {
         NNCA_LAUNCH_CHECK();
 
         // M2L items: the targets of one parent's children (their pivots are
-        // contiguous) in items of at most M2L_GROUP_TARGETS, split at multiples of
-        // M2L_WARP_TARGETS; one staging plan per parent
+        // contiguous) in items of M2L_GROUP_TARGETS and a remainder; one staging
+        // plan per parent
         std::vector<int32_t> hchb(nc), hche(nc);
         NNCA_CUDA(cudaMemcpy(hchb.data(), h->cch_beg, nc * sizeof(int32_t), cudaMemcpyDeviceToHost));
         NNCA_CUDA(cudaMemcpy(hche.data(), h->cch_end, nc * sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -1240,10 +1240,8 @@ void build_finish(Handle *h) {
             }
             const int slot = (int)parents.size();
             parents.push_back((int32_t)P);
-            const int64_t WT = M2L_WARP_TARGETS;
-            const int64_t nw = (T + WT - 1) / WT, k = (nw + M2L_GROUP_WARPS - 1) / M2L_GROUP_WARPS;
-            for (int64_t i = 0; i < k; ++i) {
-                const int64_t t0 = WT * (i * nw / k), t1 = std::min<int64_t>(T, WT * ((i + 1) * nw / k));
+            for (int64_t t0 = 0; t0 < T; t0 += M2L_GROUP_TARGETS) {
+                const int64_t t1 = std::min<int64_t>(T, t0 + M2L_GROUP_TARGETS);
                 groups.push_back({work * (t1 - t0) / T, slot, (int)t0, (int)(t1 - t0)});
             }
         }

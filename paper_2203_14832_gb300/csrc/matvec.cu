@@ -826,8 +826,9 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group(KParams kp, con
         if (wl == pw && kprod < kend) stage_load(cur, plan, plan_sh, kprod, kend);
         // this warp's cw targets sit two per lane on L lanes; in a partial warp
         // G groups of L lanes split the source pairs of every cell
-        const int wj0 = t0 + wl * M2L_WARP_TARGETS, jend = t0 + nt;
-        const int cw = min(M2L_WARP_TARGETS, max(0, jend - wj0));
+        const int wt = m2l_warp_targets(nt);
+        const int wj0 = t0 + wl * wt, jend = t0 + nt;
+        const int cw = min(wt, max(0, jend - wj0));
         const int L = cw > 0 ? (cw + 1) / 2 : 32;
         const int G = min(16, 32 / L);
         const int grp = lane / L, ti = lane - grp * L;
@@ -1551,8 +1552,9 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group_rhs(KParams kp,
         int kprod = item.z, kcons = item.z;
         StageCursor cur;
         if (wl == pw && kprod < kend) stage_load(cur, plan, plan_sh, kprod, kend);
-        const int wj0 = t0 + wl * M2L_WARP_TARGETS, jend = t0 + nt;
-        const int cw = min(M2L_WARP_TARGETS, max(0, jend - wj0));
+        const int wt = m2l_warp_targets(nt);
+        const int wj0 = t0 + wl * wt, jend = t0 + nt;
+        const int cw = min(wt, max(0, jend - wj0));
         const int L = cw > 0 ? (cw + 1) / 2 : 32;
         const int G = min(16, 32 / L);
         const int grp = lane / L, ti = lane - grp * L;
@@ -1700,19 +1702,25 @@ __device__ __forceinline__ void m2l_sym_pairs(const KParams &kp, const float4 (*
 // Column sums of one chunk: the transpose buffer holds, per target lane t < L
 // (row t, stride rs), the column values of the chunk's np2 source pairs. Lane
 // (h, p) sums pair p over one half of the rows, in row order; the halves are
-// added (half 0 + half 1) and written as the pair's two column sums.
-__device__ __forceinline__ void m2l_sym_columns(const f2 *cbuf, int rs, int L, int G, int np2, int lane, f2 *out) {
+// added (half 0 + half 1) and written as the pair's two column sums. LL > 0:
+// L = LL rows with G = 32 / LL groups (row stride 16 G + 1), unrolled.
+template <int LL>
+__device__ __forceinline__ void m2l_sym_columns(const f2 *cbuf, int rs, int L, int np2, int lane, f2 *out) {
     const int h = lane >> 4, pl = lane & 15;
     for (int pb = 0; pb < np2; pb += 16) {
         const int p = pb + pl;
         f2 s0 = 0ull, s1 = 0ull;
         if (p < np2) {
-            if (G == 1 && L == 32) {   // full warp: rows 16 h .. 16 h + 15, stride 2 M2L_FOLD + 1
-                const f2 *c = cbuf + 16 * h * (2 * M2L_FOLD + 1) + p;
+            if (LL > 0) {
+                constexpr int RS = LL > 0 ? 2 * M2L_FOLD * (32 / (LL > 0 ? LL : 1)) + 1 : 1;
+                constexpr int HR = LL > 1 ? LL / 2 : 1;   // rows per half
+                if (LL > 1 || h == 0) {
+                    const f2 *c = cbuf + h * HR * RS + p;
 #pragma unroll
-                for (int k = 0; k < 16; k += 2) {
-                    s0 = f2_add(s0, c[k * (2 * M2L_FOLD + 1)]);
-                    s1 = f2_add(s1, c[(k + 1) * (2 * M2L_FOLD + 1)]);
+                    for (int k = 0; k < HR; k += 2) {
+                        s0 = f2_add(s0, c[k * RS]);
+                        if (k + 1 < HR) s1 = f2_add(s1, c[(k + 1) * RS]);
+                    }
                 }
             } else {
                 const int hl = (L + 1) >> 1, r0 = h ? hl : 0, r1 = h ? L : hl;
@@ -1723,6 +1731,19 @@ __device__ __forceinline__ void m2l_sym_columns(const f2 *cbuf, int rs, int L, i
         const f2 other = __shfl_xor_sync(0xffffffffu, mine, 16);
         if (h == 0 && p < np2) out[p] = f2_add(mine, other);
     }
+}
+
+__device__ __forceinline__ void m2l_sym_columns_any(const f2 *cbuf, int rs, int L, int G, int np2, int lane, f2 *out) {
+    if (L * G == 32) {
+        switch (L) {
+        case 32: m2l_sym_columns<32>(cbuf, rs, L, np2, lane, out); return;
+        case 16: m2l_sym_columns<16>(cbuf, rs, L, np2, lane, out); return;
+        case 8: m2l_sym_columns<8>(cbuf, rs, L, np2, lane, out); return;
+        case 4: m2l_sym_columns<4>(cbuf, rs, L, np2, lane, out); return;
+        default: break;
+        }
+    }
+    m2l_sym_columns<0>(cbuf, rs, L, np2, lane, out);
 }
 
 template <int KIND>
@@ -1765,8 +1786,9 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_sym(KParams kp, const
         int kprod = item.z, kcons = item.z;
         StageCursor cur;
         if (wl == pw && kprod < kend) stage_load(cur, plan, plan_sh, kprod, kend);
-        const int wj0 = t0 + wl * M2L_WARP_TARGETS, jend = t0 + nt;
-        const int cw = min(M2L_WARP_TARGETS, max(0, jend - wj0));
+        const int wt = m2l_warp_targets(nt);
+        const int wj0 = t0 + wl * wt, jend = t0 + nt;
+        const int cw = min(wt, max(0, jend - wj0));
         const int L = cw > 0 ? (cw + 1) / 2 : 32;
         const int G = min(16, 32 / L);
         const int grp = lane / L, ti = lane - grp * L;
@@ -1829,7 +1851,7 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_sym(KParams kp, const
                         if (onb) two_sum_add(Tb.sum, Tb.comp, pb.x + pb.y);
                     }
                     __syncwarp();
-                    m2l_sym_columns(cbuf, rs, L, G, c1 - c0, lane, reinterpret_cast<f2 *>(cwb) + c0);
+                    m2l_sym_columns_any(cbuf, rs, L, G, c1 - c0, lane, reinterpret_cast<f2 *>(cwb) + c0);
                     __syncwarp();
                 }
             }

@@ -161,13 +161,23 @@ __device__ __forceinline__ float kern32_r2(const KParams &kp, float r2) {
 inline bool kernel_is_radial(int kind) { return kind != NNCA_K_SEPARABLE && kind != NNCA_K_POLY2; }
 
 // The FP32 M2L runs one thread block of M2L_GROUP_WARPS warps per group of
-// sibling target cells, M2L_WARP_TARGETS consecutive targets per warp (two per
-// lane); a group item holds at most M2L_GROUP_TARGETS targets. Source cells
+// sibling target cells; a group item holds at most M2L_GROUP_TARGETS
+// consecutive targets (items of M2L_GROUP_TARGETS and a remainder), and its
+// warps take m2l_warp_targets(targets) consecutive targets each (two per lane
+// on half as many lanes; the warp's other lane groups split the sources), so
+// that the four warps of an item stay busy for about the same time. Source cells
 // arrive in staging rounds of at most M2L_STAGE_RECS cells and M2L_STAGE_CAP
 // sources (padded counts), which bounds the largest rank it takes.
 constexpr int M2L_GROUP_WARPS = 4;
 constexpr int M2L_WARP_TARGETS = 64;
 constexpr int M2L_GROUP_TARGETS = M2L_WARP_TARGETS * M2L_GROUP_WARPS;
+// targets per warp of an item of nt targets: the least power of two (at least
+// 2) with four warps covering nt, at most M2L_WARP_TARGETS
+__host__ __device__ inline int m2l_warp_targets(int nt) {
+    int s = 2;
+    while (s * M2L_GROUP_WARPS < nt && s < M2L_WARP_TARGETS) s <<= 1;
+    return s;
+}
 constexpr int M2L_STAGE_CAP = 512;
 constexpr int M2L_STAGE_RECS = 32;
 constexpr int M2L_STAGE_BUFS = 4;
