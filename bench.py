@@ -192,9 +192,15 @@ def cpu_baseline(threads: int) -> dict:
     for _ in range(reps):
         h.matvec(x)
     t = (time.perf_counter() - t0) / reps
+    # the same product on one thread (one product)
+    t1 = time.perf_counter()
+    h.matvec(x, nthreads=1)
+    t1 = time.perf_counter() - t1
     return {"value": n * nrhs / t, "unit": "points/s", "cores": threads, "kind": "oracle",
+            "value_1thread": n * nrhs / t1,
             "sample": f"FP64 oracle H2 product (on-the-fly form) on {n} points of the same recipe "
-                      f"(oracle build {tb:.1f} s untimed), mean of {reps} products"}
+                      f"(oracle build {tb:.1f} s untimed), mean of {reps} products; value_1thread: one "
+                      f"product on one thread"}
 
 
 def run_reference(args):
@@ -376,6 +382,9 @@ def run_ours(args):
                      "unit": "G kernel evaluations/s", "frac": achieved / peak_gpair, "traffic": traffic,
                      "peak_note": f"one MUFU rsqrt per evaluation: {MUFU_PER_CLK_SM}/clk/SM x {SMS} SMs x "
                                   f"{sm_max:.0f} MHz",
+                     "pairs_served_per_s_frac": st["m2l_pairs"] / (m2l_ms / 1e3) / 1e9 / peak_gpair,
+                     "pairs_note": "symmetric form: each evaluation feeds two ordered pivot pairs (a row and "
+                                   "a column sum); this fraction counts those pairs against the same peak",
                      "traffic_note": "DRAM bytes of one M2L launch, ncu at N=131072 scaled by N"},
         "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": N * nrhs * 8,
                 "d2h_bytes_per_step": N * nrhs * 8, "matches_device_result": e2e_ok},

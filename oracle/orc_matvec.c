@@ -26,6 +26,7 @@
  * for j == i, summed in ascending j.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdlib.h>
 #include <string.h>
 #include "oracle.h"
@@ -78,7 +79,9 @@ int orc_assemble(orc_h2 *h) {
 }
 
 int orc_h2_matvec(const orc_h2 *h, const double *x, double *y, long nrhs, long ld, int form, int nthreads) {
-    (void)nthreads;
+    /* nthreads > 0: that many threads; each output is summed by one thread in a
+     * fixed order, so the result does not depend on it */
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
     if (form == 1 && !h->s_blk) return -1;
     const long n = h->n, nc = h->ncell, npiv = h->piv_off[nc];
     double *xs = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
@@ -91,7 +94,7 @@ int orc_h2_matvec(const orc_h2 *h, const double *x, double *y, long nrhs, long l
         for (long t = 0; t < npiv; ++t) { w[t] = 0.0; u[t] = 0.0; }
         /* step 2: upward pass */
         for (int l = h->kappa; l >= h->lmin; --l) {
-            #pragma omp parallel for schedule(dynamic, 16)
+            #pragma omp parallel for num_threads(nt) schedule(dynamic, 16)
             for (long B = h->level_base[l]; B < h->level_base[l + 1]; ++B) {
                 const long r = h->piv_off[B + 1] - h->piv_off[B];
                 const double *op = h->op + h->op_off[B];
@@ -117,7 +120,7 @@ int orc_h2_matvec(const orc_h2 *h, const double *x, double *y, long nrhs, long l
             }
         }
         /* step 3: transverse pass */
-        #pragma omp parallel for schedule(dynamic, 16)
+        #pragma omp parallel for num_threads(nt) schedule(dynamic, 16)
         for (long X = h->level_base[h->lmin <= h->kappa ? h->lmin : h->kappa + 1]; X < nc; ++X) {
             const long *tX = h->piv_row + h->piv_off[X];
             const long rX = h->piv_off[X + 1] - h->piv_off[X];
@@ -140,7 +143,7 @@ int orc_h2_matvec(const orc_h2 *h, const double *x, double *y, long nrhs, long l
         }
         /* step 4: downward pass, levels top-down, then leaves */
         for (int l = h->lmin + 1; l <= h->kappa; ++l) {
-            #pragma omp parallel for schedule(dynamic, 16)
+            #pragma omp parallel for num_threads(nt) schedule(dynamic, 16)
             for (long B = h->level_base[l]; B < h->level_base[l + 1]; ++B) {
                 const long P = h->cpar[B];
                 const long rP = h->piv_off[P + 1] - h->piv_off[P];
@@ -159,7 +162,7 @@ int orc_h2_matvec(const orc_h2 *h, const double *x, double *y, long nrhs, long l
         }
         for (long i = 0; i < n; ++i) ys[i] = 0.0;
         if (h->lmin <= h->kappa) {
-            #pragma omp parallel for schedule(dynamic, 16)
+            #pragma omp parallel for num_threads(nt) schedule(dynamic, 16)
             for (long B = h->level_base[h->kappa]; B < h->level_base[h->kappa + 1]; ++B) {
                 const long r = h->piv_off[B + 1] - h->piv_off[B];
                 const double *op = h->op + h->op_off[B];
@@ -172,7 +175,7 @@ int orc_h2_matvec(const orc_h2 *h, const double *x, double *y, long nrhs, long l
             }
         }
         /* step 5: near field */
-        #pragma omp parallel for schedule(dynamic, 16)
+        #pragma omp parallel for num_threads(nt) schedule(dynamic, 16)
         for (long X = h->level_base[h->kappa]; X < h->level_base[h->kappa + 1]; ++X) {
             for (long a = h->cbeg[X]; a < h->cend[X]; ++a) {
                 double s = 0.0;
