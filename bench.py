@@ -352,9 +352,11 @@ def run_ours(args):
     achieved = evals / (m2l_ms / 1e3) / 1e9
     traffic = None
     tf = os.path.join(ROOT, "profiles", ("m2l_sym" if sym else "m2l_group") + "_traffic_invr3d.json")
+    traffic_note = None
     if os.path.exists(tf) and w.name == "invr3d_1m" and w.n == 1 << 20:
         try:
-            traffic = json.load(open(tf)).get("bytes_per_launch")
+            tj = json.load(open(tf))
+            traffic, traffic_note = tj.get("bytes_per_launch"), tj.get("note")
         except Exception:
             traffic = None
 
@@ -385,7 +387,8 @@ def run_ours(args):
                      "pairs_served_per_s_frac": st["m2l_pairs"] / (m2l_ms / 1e3) / 1e9 / peak_gpair,
                      "pairs_note": "symmetric form: each evaluation feeds two ordered pivot pairs (a row and "
                                    "a column sum); this fraction counts those pairs against the same peak",
-                     "traffic_note": "DRAM bytes of one M2L launch, ncu at N=131072 scaled by N"},
+                     "traffic_note": ("DRAM bytes read + written by one M2L launch: " + traffic_note) if traffic_note
+                     else "no full-size ncu DRAM figure for this kernel and workload"},
         "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": N * nrhs * 8,
                 "d2h_bytes_per_step": N * nrhs * 8, "matches_device_result": e2e_ok},
         "gpu_launches": int(st_prof["launches_per_product"]) * args.steps,
