@@ -1516,7 +1516,32 @@ void build_finish(Handle *h) {
                 if (!v.empty())
                     NNCA_CUDA(cudaMemcpy(h->near_items[t], v.data(), v.size() * sizeof(int4), cudaMemcpyHostToDevice));
             }
-            h->near_next = dalloc<int>(h, 2);
+            h->near_next = dalloc<int>(h, 3);
+            // items of the four-right-hand-side kernel: two targets per lane, leaves of
+            // more than 64 points in pieces of at most 64 targets
+            std::vector<std::pair<int64_t, int4>> it4;
+            for (int64_t c = leaf0; c < leaf1; ++c) {
+                const int64_t nb = hce[c] - hcb[c];
+                const int64_t pieces = (nb + 63) / 64;
+                for (int64_t p = 0; p < pieces; ++p) {
+                    const int64_t f = nb * p / pieces, cnt = nb * (p + 1) / pieces - f;
+                    const int64_t L = (cnt + 1) / 2;
+                    const int G = (int)std::min<int64_t>(16, 32 / L);
+                    it4.push_back({hp[c - leaf0] * cnt / std::max<int64_t>(nb, 1),
+                                   make_int4((int)c, (int)f | (int)(cnt << 16) | (G << 24), (int)roff[c - leaf0],
+                                             (int)(roff[c - leaf0 + 1] - roff[c - leaf0]))});
+                }
+            }
+            std::stable_sort(it4.begin(), it4.end(),
+                             [](const std::pair<int64_t, int4> &x, const std::pair<int64_t, int4> &y) { return x.first > y.first; });
+            std::vector<int4> v4;
+            for (auto &p : it4) v4.push_back(p.second);
+            h->n_near_items4 = (int)v4.size();
+            h->near_items4 = dalloc<int4>(h, v4.size());
+            if (!v4.empty())
+                NNCA_CUDA(cudaMemcpy(h->near_items4, v4.data(), v4.size() * sizeof(int4), cudaMemcpyHostToDevice));
+            h->pw4 = dalloc<float4>(h, 2 * (size_t)npairs);
+            NNCA_CUDA(cudaMemsetAsync(h->pw4, 0, 2 * (size_t)npairs * sizeof(float4), s));
         }
     }
     {

@@ -766,6 +766,16 @@ __device__ __forceinline__ f2 group_pair(const KParams &kp, const ulonglong2 &A,
     return f2_fma(KF2<KIND, false>::eval(kp, r2), B.y, acc);
 }
 
+// f(|s - t|^2) of a packed pair of sources
+template <int KIND>
+__device__ __forceinline__ f2 group_f(const KParams &kp, const ulonglong2 &A, const ulonglong2 &B, f2 tx, f2 ty, f2 tz) {
+    const f2 dx = f2_sub(A.x, tx), dy = f2_sub(A.y, ty), dz = f2_sub(B.x, tz);
+    f2 r2 = f2_mul(dx, dx);
+    r2 = f2_fma(dy, dy, r2);
+    r2 = f2_fma(dz, dz, r2);
+    return KF2<KIND, false>::eval(kp, r2);
+}
+
 // the source pairs q0, q0 + step, ... below q1 (pairs taken two at a time) of one
 // staged cell against two targets; FULL: the whole warp, step 2
 template <int KIND, int FULL>
@@ -1305,6 +1315,243 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_near_group(KParams kp, cons
         for (unsigned r = R; r < Rp; ++r) mbar_wait(&W.full[r % NEAR_BUFS], (r / NEAR_BUFS) & 1);
 }
 
+// ---- near field of M2L_RHS right-hand sides at once (FP32) -----------------------
+// The same staging and pair arithmetic as k_near_group with two targets per lane;
+// each kernel value feeds the four right-hand sides' accumulators, whose source
+// weights come from pw4 (two float4 per point pair, L2-resident) beside the
+// staged coordinates. L2P of the four and the diagonal term follow in the warp.
+struct NearTarget4 {
+    bool act = false;
+    int i = 0;
+    f2 xh = 0ull, yh = 0ull, zh = 0ull, xl = 0ull, yl = 0ull, zl = 0ull;
+    float sum[M2L_RHS] = {0.f, 0.f, 0.f, 0.f}, comp[M2L_RHS] = {0.f, 0.f, 0.f, 0.f};
+};
+
+__device__ __forceinline__ void near_target4(NearTarget4 &T, bool act, int i, const float4 *xh4, const float4 *xl4) {
+    T.act = act;
+    T.i = i;
+    if (!act) return;
+    const float4 h = xh4[i], l = xl4[i];
+    T.xh = f2_pack(h.x, h.x);
+    T.yh = f2_pack(h.y, h.y);
+    T.zh = f2_pack(h.z, h.z);
+    T.xl = f2_pack(l.x, l.x);
+    T.yl = f2_pack(l.y, l.y);
+    T.zl = f2_pack(l.z, l.z);
+}
+
+// fold a cell's partial sums (acc[k][r]) into the compensated totals
+__device__ __forceinline__ void near4_fold(NearTarget4 (&T)[2], f2 (&acc)[2][M2L_RHS]) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int r = 0; r < M2L_RHS; ++r) {
+            const float2 p = f2_unpack(acc[k][r]);
+            two_sum_add(T[k].sum[r], T[k].comp[r], p.x + p.y);
+        }
+}
+
+// an adjacent cell (hi/lo pairs at P[4 q], weights of pair q at W[2 q]): this
+// lane's group takes pairs g, g + G, ...
+template <int KIND, bool SAFE>
+__device__ __forceinline__ void near4_cell(const KParams &kp, const float4 *P, const float4 *W, int np, int g, int G,
+                                           NearTarget4 (&T)[2]) {
+    f2 acc[2][M2L_RHS];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int r = 0; r < M2L_RHS; ++r) acc[k][r] = 0ull;
+    for (int q = g; q < np; q += G) {
+        const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(&P[4 * q]);
+        const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(&P[4 * q + 1]);
+        const ulonglong2 C = *reinterpret_cast<const ulonglong2 *>(&P[4 * q + 2]);
+        const ulonglong2 D = *reinterpret_cast<const ulonglong2 *>(&P[4 * q + 3]);
+        const ulonglong2 w01 = __ldg(reinterpret_cast<const ulonglong2 *>(&W[2 * q]));
+        const ulonglong2 w23 = __ldg(reinterpret_cast<const ulonglong2 *>(&W[2 * q + 1]));
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const f2 dx = f2_add(f2_sub(A.x, T[k].xh), f2_sub(C.x, T[k].xl));
+            const f2 dy = f2_add(f2_sub(A.y, T[k].yh), f2_sub(C.y, T[k].yl));
+            const f2 dz = f2_add(f2_sub(B.x, T[k].zh), f2_sub(D.x, T[k].zl));
+            f2 r2 = f2_mul(dx, dx);
+            r2 = f2_fma(dy, dy, r2);
+            r2 = f2_fma(dz, dz, r2);
+            const f2 f = KF2<KIND, SAFE>::eval(kp, r2);
+            acc[k][0] = f2_fma(f, w01.x, acc[k][0]);
+            acc[k][1] = f2_fma(f, w01.y, acc[k][1]);
+            acc[k][2] = f2_fma(f, w23.x, acc[k][2]);
+            acc[k][3] = f2_fma(f, w23.y, acc[k][3]);
+        }
+    }
+    near4_fold(T, acc);
+}
+
+// a leaf at least one leaf away (pairs relative to its centre at P[2 q])
+template <int KIND>
+__device__ __forceinline__ void near4_cell_far(const KParams &kp, const float4 *P, const float4 *W, int np, int g,
+                                               int G, float4 ch, float4 cl, NearTarget4 (&T)[2]) {
+    f2 tx[2], ty[2], tz[2], acc[2][M2L_RHS];
+    {
+        const f2 hx = f2_pack(ch.x, ch.x), hy = f2_pack(ch.y, ch.y), hz = f2_pack(ch.z, ch.z);
+        const f2 lx = f2_pack(cl.x, cl.x), ly = f2_pack(cl.y, cl.y), lz = f2_pack(cl.z, cl.z);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            tx[k] = f2_add(f2_sub(T[k].xh, hx), f2_sub(T[k].xl, lx));
+            ty[k] = f2_add(f2_sub(T[k].yh, hy), f2_sub(T[k].yl, ly));
+            tz[k] = f2_add(f2_sub(T[k].zh, hz), f2_sub(T[k].zl, lz));
+#pragma unroll
+            for (int r = 0; r < M2L_RHS; ++r) acc[k][r] = 0ull;
+        }
+    }
+    for (int q = g; q < np; q += G) {
+        const ulonglong2 A = *reinterpret_cast<const ulonglong2 *>(&P[2 * q]);
+        const ulonglong2 B = *reinterpret_cast<const ulonglong2 *>(&P[2 * q + 1]);
+        const ulonglong2 w01 = __ldg(reinterpret_cast<const ulonglong2 *>(&W[2 * q]));
+        const ulonglong2 w23 = __ldg(reinterpret_cast<const ulonglong2 *>(&W[2 * q + 1]));
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const f2 f = group_f<KIND>(kp, A, B, tx[k], ty[k], tz[k]);
+            acc[k][0] = f2_fma(f, w01.x, acc[k][0]);
+            acc[k][1] = f2_fma(f, w01.y, acc[k][1]);
+            acc[k][2] = f2_fma(f, w23.x, acc[k][2]);
+            acc[k][3] = f2_fma(f, w23.y, acc[k][3]);
+        }
+    }
+    near4_fold(T, acc);
+}
+
+// items: (leaf, first target | targets << 16 | groups << 24, first record, records);
+// u, xt64: M2L_RHS rows of npiv and N; y: M2L_RHS rows of ld
+template <int KIND, class TO>
+__global__ void __launch_bounds__(32 * NEAR_WARPS) k_near_rhs(KParams kp, const int4 *items, int nitems,
+                                                             int *next_item, const int4 *plan, const int32_t *cbeg,
+                                                             const int32_t *piv_off, const int64_t *op_off,
+                                                             const double *op, const double *u, int64_t npiv,
+                                                             const float4 *xh4, const float4 *xl4, const float4 *chi,
+                                                             const float4 *clo, const float4 *ppk, const float4 *ppl,
+                                                             const float4 *pw4, const double *xt64, int64_t N,
+                                                             const int32_t *perm, TO *y, int64_t ld, unsigned *status) {
+    __shared__ __align__(128) NearWarpSmem Sm[NEAR_WARPS];
+    __shared__ int pq[NEAR_WARPS][NEAR_BUFS][NEAR_RECS];   // first global pair of each staged record
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    NearWarpSmem &W = Sm[wl];
+    if (lane == 0) {
+        for (int b = 0; b < NEAR_BUFS; ++b) mbar_init(&W.full[b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const float k0 = KF<KIND>::f32(kp, 0.f);
+    unsigned R = 0, Rp = 0;
+    bool failed = false;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = atomicAdd(next_item, 1);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= nitems || failed) break;
+        const int4 item = items[it];
+        const int B = item.x, f0 = item.y & 0xffff, c = (item.y >> 16) & 0xff, G = (item.y >> 24) & 0x1f;
+        const int kend = item.z + item.w;
+        const int L = (c + 1) / 2;
+        const int g = lane / L, ti = lane - g * L;
+        const bool live = g < G;
+        const int i0 = cbeg[B] + f0;
+        NearTarget4 T[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) near_target4(T[k], live && ti * 2 + k < c, i0 + ti * 2 + k, xh4, xl4);
+        int kprod = item.z, kcons = item.z;
+        NearCursor cur;
+        near_load(cur, plan, chi, clo, kprod, kend);
+        while (kcons < kend) {
+            while (kprod < kend && Rp <= R + NEAR_BUFS - 2) {
+                const int b = Rp % NEAR_BUFS;
+                if (lane < NEAR_RECS) pq[wl][b][lane] = cur.r.y;
+                const int kn = near_stage(W, b, cur, kprod, kend, ppk, ppl, status);
+                if (kn < 0) {
+                    kprod = kend;
+                    failed = true;
+                    break;
+                }
+                kprod = kn;
+                ++Rp;
+                near_load(cur, plan, chi, clo, kprod, kend);
+            }
+            if (failed) break;
+            const int b = R % NEAR_BUFS;
+            if (!mbar_wait_warp(&W.full[b], (R / NEAR_BUFS) & 1)) {
+                if (lane == 0) atomicOr(status, DEV_WAIT_TIMEOUT);
+                failed = true;
+                break;
+            }
+            const int nrec = W.nrec[b];
+            if (live)
+                for (int e = 0; e < nrec; ++e) {
+                    const int hw = W.hdr[b][e];
+                    const float4 *P = &W.u[b][hw & 0x7ff];
+                    const float4 *Wt = pw4 + 2 * (int64_t)pq[wl][b][e];
+                    const int np = (hw >> 11) & 0x7ff;
+                    if (!((hw >> 23) & 1)) near4_cell_far<KIND>(kp, P, Wt, np, g, G, W.ch[b][e], W.cl[b][e], T);
+                    else if ((hw >> 22) & 1) near4_cell<KIND, true>(kp, P, Wt, np, g, G, T);
+                    else near4_cell<KIND, false>(kp, P, Wt, np, g, G, T);
+                }
+            __syncwarp();
+            ++R;
+            kcons += nrec;
+        }
+        if (failed) break;
+        for (int gg = 1; gg < G; ++gg) {
+            const int srcl = min(ti + gg * L, 31);
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+#pragma unroll
+                for (int r = 0; r < M2L_RHS; ++r) {
+                    const float so = __shfl_sync(0xffffffffu, T[k].sum[r], srcl);
+                    const float co = __shfl_sync(0xffffffffu, T[k].comp[r], srcl);
+                    if (g == 0) {
+                        two_sum_add(T[k].sum[r], T[k].comp[r], so);
+                        T[k].comp[r] += co;
+                    }
+                }
+        }
+        if (g == 0) {
+            // L2P of the four in FP64 (one pass over the row of U_B), then the diagonal
+            const int rk = piv_off[B + 1] - piv_off[B];
+            const int64_t ub = piv_off[B];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (!T[k].act) continue;
+                const double *Urow = op + op_off[B] + (int64_t)(T[k].i - cbeg[B]) * rk;
+                double far[M2L_RHS] = {0.0, 0.0, 0.0, 0.0};
+                for (int bb = 0; bb < rk; ++bb) {
+                    const double ue = Urow[bb];
+#pragma unroll
+                    for (int r = 0; r < M2L_RHS; ++r) far[r] = fma(ue, u[r * npiv + ub + bb], far[r]);
+                }
+#pragma unroll
+                for (int r = 0; r < M2L_RHS; ++r) {
+                    const double near = (double)T[k].sum[r] + (double)T[k].comp[r];
+                    const double yv =
+                        far[r] + kp.s * near + (kp.diag - kp.s * (double)k0) * xt64[r * N + T[k].i];
+                    y[r * ld + perm[T[k].i]] = (TO)yv;
+                }
+            }
+        }
+    }
+    if (lane == 0)
+        for (unsigned r = R; r < Rp; ++r) mbar_wait(&W.full[r % NEAR_BUFS], (r / NEAR_BUFS) & 1);
+}
+
+// the four right-hand sides' FP32 weights of every leaf point into pw4
+__global__ void k_near_weights4(int64_t N, const double *xt, float *pw4, const int32_t *leaf_of, const int32_t *cbeg,
+                                const int32_t *ppk_off) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int B = leaf_of[i];
+        const int64_t j = i - cbeg[B];
+        const int64_t q = (int64_t)ppk_off[B] + (j >> 1);
+#pragma unroll
+        for (int r = 0; r < M2L_RHS; ++r) pw4[8 * q + (r >> 1) * 4 + (r & 1) * 2 + (j & 1)] = (float)xt[r * N + i];
+    }
+}
+
 // ---- leaves: L2P + P2P, FP64 -------------------------------------------------
 template <int KIND, int NR, class TO>
 __global__ void __launch_bounds__(32 * MV_WARPS) k_leaf_f64(KParams kp, int d, const int32_t *leaves, int64_t nleaf,
@@ -1503,15 +1750,6 @@ __device__ __forceinline__ int m2l_stage_rhs(M2lRhsSmem &S, int b, unsigned use,
     return k + nrec;
 }
 
-// f(|s - t|^2) of a packed pair of sources
-template <int KIND>
-__device__ __forceinline__ f2 group_f(const KParams &kp, const ulonglong2 &A, const ulonglong2 &B, f2 tx, f2 ty, f2 tz) {
-    const f2 dx = f2_sub(A.x, tx), dy = f2_sub(A.y, ty), dz = f2_sub(B.x, tz);
-    f2 r2 = f2_mul(dx, dx);
-    r2 = f2_fma(dy, dy, r2);
-    r2 = f2_fma(dz, dz, r2);
-    return KF2<KIND, false>::eval(kp, r2);
-}
 
 template <int KIND>
 __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group_rhs(KParams kp, const int4 *items, int nitems,
@@ -2076,6 +2314,24 @@ void launch_leaf_f32(Handle *h, const double *op, const double *u, const float *
     }
 }
 
+// the near field of M2L_RHS right-hand sides (u, xt64: M2L_RHS rows; y: rows of ld)
+template <int KIND, class TO>
+void launch_near_rhs(Handle *h, const double *op, const double *u, const double *xt64, TO *y, int64_t ld) {
+    int dev = 0, nsm = 152, per_sm = 1;
+    NNCA_CUDA(cudaGetDevice(&dev));
+    NNCA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    NNCA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_near_rhs<KIND, TO>, 32 * NEAR_WARPS, 0));
+    const int n = h->n_near_items4;
+    const int64_t warps = (int64_t)nsm * std::max(1, per_sm) * NEAR_WARPS;
+    const unsigned g = (unsigned)((std::min<int64_t>(n, warps) + NEAR_WARPS - 1) / NEAR_WARPS);
+    NNCA_CUDA(cudaMemsetAsync(h->near_next + 2, 0, sizeof(int), h->stream));
+    k_near_rhs<KIND, TO><<<g, 32 * NEAR_WARPS, 0, h->stream>>>(
+        h->kp, h->near_items4, n, h->near_next + 2, h->near_plan, h->cbeg, h->piv_off, h->op_off, op, u, h->npiv,
+        h->xh4, h->xl4, h->chi4, h->clo4, h->ppk, h->ppl, h->pw4, xt64, h->n, h->perm, y, ld, h->dev_status);
+    NNCA_LAUNCH_CHECK();
+    ++h->launches;
+}
+
 void ensure_workspace(Handle *h, int64_t nrhs) {
     if (h->ws && h->ws_nrhs >= nrhs) return;
     if (h->ws) {
@@ -2173,6 +2429,13 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
             npiv, h->xs, N, xt, h->perm, yout, ld);
     } else if (FP32 && NR == 1) {
         launch_leaf_f32<KIND, TO>(h, op, u, xt32, xt, yout);
+    } else if (FP32 && NR == M2L_RHS && h->near_packed && h->n_near_items4) {
+        // the near field of the four right-hand sides in one pass
+        k_near_weights4<<<grid_for(N, 256), 256, 0, s>>>(N, xt, reinterpret_cast<float *>(h->pw4), h->leaf_of, h->cbeg,
+                                                         h->ppk_off);
+        NNCA_LAUNCH_CHECK();
+        ++h->launches;
+        launch_near_rhs<KIND, TO>(h, op, u, xt, yout, ld);
     } else if (FP32) {
         // the near field one right-hand side at a time
         for (int r = 0; r < NR; ++r) {

@@ -311,6 +311,14 @@ struct Handle {
     int n_near_items[2] = {0, 0};
     int *near_next = nullptr;                    // [2] item counters
     bool near_packed = false;     // false: leaves too large, the ring kernel serves them
+    // FP32 near field of M2L_RHS right-hand sides at once: the weights of every
+    // packed point pair for the four, [w0(p0) w0(p1) w1(p0) w1(p1)][w2(p0) w2(p1)
+    // w3(p0) w3(p1)] (2 float4 per pair, pairs as in ppk), and items of at most
+    // 64 targets (leaf, first target | targets << 16 | groups << 24, first record,
+    // records), two targets per lane
+    float4 *pw4 = nullptr;
+    int4 *near_items4 = nullptr;
+    int n_near_items4 = 0;
     const char *m2l_fp32_unsupported = nullptr;   // why the FP32 M2L cannot run, or null
     int4 *m2l_plan = nullptr;
     float4 *m2l_plan_sh = nullptr;   // per plan record: c_Y - c_P rounded to float
