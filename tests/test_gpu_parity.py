@@ -315,3 +315,25 @@ def test_fp32_multi_rhs(gpu, orc):
         assert rel(Y32[r], y1) < 1e-6
     assert g.stats()["device_status"] & (2 | 16) == 0
     g.close()
+
+
+@pytest.mark.parametrize("wl,n,kw", [("gauss_mix_256k", 12000, {"leaf_size": 32}), ("sphere_512k", 12000, {})])
+def test_fp32_four_rhs(gpu, orc, wl, n, kw):
+    """A pass of four right-hand sides (M2L and near field each evaluating a pair once for
+    the four) on the Gaussian kernel and on the sphere's scaled 1/r with its diagonal:
+    every column within 1e-6 of the oracle's FP64 product and of the one-RHS FP32 product."""
+    import torch
+    w = W.WORKLOADS[wl].scaled(n)
+    P = w.make_points()
+    gcfg, ocfg = configs(gpu, orc, w, **kw)
+    g = gpu.H2(torch.as_tensor(P, device="cuda"), gcfg)
+    o = orc.H2(P, ocfg)
+    X = W.vector_normal(n, 31, nrhs=4)
+    Y32 = g.matvec(torch.as_tensor(X, device="cuda"), gpu.PREC_FP32).cpu().numpy()
+    for r in range(4):
+        yo = o.matvec(X[r].copy())
+        y1 = g.matvec(torch.as_tensor(X[r].copy(), device="cuda"), gpu.PREC_FP32).cpu().numpy()
+        assert rel(Y32[r], yo) < 1e-6
+        assert rel(Y32[r], y1) < 1e-6
+    assert g.stats()["device_status"] & (2 | 16) == 0
+    g.close()
