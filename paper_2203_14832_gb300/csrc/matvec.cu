@@ -596,15 +596,19 @@ struct M2lGroupSmem {
 // M2L_SYM_CAP sources), each warp's column sums of the rounds in flight, a
 // per-warp transpose buffer for the column sums of one chunk, and per buffer
 // the round's first column slot, its sources and the warps done with it.
+// three staging buffers (one round of lookahead): with 1/r the block then fits
+// five times per SM (96 registers per thread, 43 KB of shared memory)
+constexpr int M2L_SYM_BUFS = 3;
+constexpr int M2L_SYM_AHEAD = M2L_SYM_BUFS - 2;
 constexpr int M2L_SYM_COLBUF = 32 * (2 * M2L_FOLD + 1);   // float2 per warp: L rows of 2 M2L_FOLD G + 1, L G <= 32
 struct M2lSymSmem {
-    float4 src[M2L_STAGE_BUFS][M2L_SYM_CAP / 2][2];
-    float colw[M2L_STAGE_BUFS][M2L_GROUP_WARPS][M2L_SYM_CAP];
+    float4 src[M2L_SYM_BUFS][M2L_SYM_CAP / 2][2];
+    float colw[M2L_SYM_BUFS][M2L_GROUP_WARPS][M2L_SYM_CAP];
     float2 colbuf[M2L_GROUP_WARPS][M2L_SYM_COLBUF];
-    int hdr[M2L_STAGE_BUFS][M2L_STAGE_RECS];
-    float4 sh[M2L_STAGE_BUFS][M2L_STAGE_RECS];
-    int nrec[M2L_STAGE_BUFS], rbase[M2L_STAGE_BUFS], rsrc[M2L_STAGE_BUFS], cnt[M2L_STAGE_BUFS];
-    unsigned long long full[M2L_STAGE_BUFS], empty[M2L_STAGE_BUFS];
+    int hdr[M2L_SYM_BUFS][M2L_STAGE_RECS];
+    float4 sh[M2L_SYM_BUFS][M2L_STAGE_RECS];
+    int nrec[M2L_SYM_BUFS], rbase[M2L_SYM_BUFS], rsrc[M2L_SYM_BUFS], cnt[M2L_SYM_BUFS];
+    unsigned long long full[M2L_SYM_BUFS], empty[M2L_SYM_BUFS];
     int2 ch_range[8];
     int item;
     int abort;
@@ -1985,7 +1989,7 @@ __device__ __forceinline__ void m2l_sym_columns_any(const f2 *cbuf, int rs, int 
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_sym(KParams kp, const int4 *items, int nitems,
+__global__ void __launch_bounds__(M2L_GROUP_THREADS, KIND == NNCA_K_INV_R ? 5 : 4) k_m2l_sym(KParams kp, const int4 *items, int nitems,
                                                              int *next_item, const int4 *plan, const float4 *plan_sh,
                                                              const int32_t *cch_beg, const int32_t *cch_end,
                                                              const int2 *prange, const float4 *pv4, const float4 *chi,
@@ -1996,7 +2000,7 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_sym(KParams kp, const
     M2lSymSmem &S = *reinterpret_cast<M2lSymSmem *>(sym_smem);
     const int tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
     if (tid == 0) {
-        for (int b = 0; b < M2L_STAGE_BUFS; ++b) {
+        for (int b = 0; b < M2L_SYM_BUFS; ++b) {
             mbar_init(&S.full[b], 1);
             mbar_init(&S.empty[b], M2L_GROUP_WARPS);
             S.cnt[b] = 0;
@@ -2042,13 +2046,13 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_sym(KParams kp, const
         const int span = 2 * M2L_FOLD * G, rs = span + 1;   // chunk (source pairs) and transpose row length
         while (kcons < kend) {
             if (wl == pw)
-                while (kprod < kend && Rp <= R + M2L_STAGE_AHEAD) {
-                    kprod = m2l_stage(S, Rp % M2L_STAGE_BUFS, Rp / M2L_STAGE_BUFS, cur, plan, plan_sh, kend, spk,
+                while (kprod < kend && Rp <= R + M2L_SYM_AHEAD) {
+                    kprod = m2l_stage(S, Rp % M2L_SYM_BUFS, Rp / M2L_SYM_BUFS, cur, plan, plan_sh, kend, spk,
                                       status);
                     ++Rp;
                 }
-            const int b = R % M2L_STAGE_BUFS;
-            if (!mbar_wait_warp(&S.full[b], (R / M2L_STAGE_BUFS) & 1)) {
+            const int b = R % M2L_SYM_BUFS;
+            if (!mbar_wait_warp(&S.full[b], (R / M2L_SYM_BUFS) & 1)) {
                 if (lane == 0) {
                     atomicOr(status, DEV_WAIT_TIMEOUT);
                     *(volatile int *)&S.abort = 1;
@@ -2133,7 +2137,7 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_sym(KParams kp, const
         }
     }
     if (wl == pw && lane == 0)
-        for (unsigned r = R; r < Rp; ++r) mbar_wait(&S.full[r % M2L_STAGE_BUFS], (r / M2L_STAGE_BUFS) & 1);
+        for (unsigned r = R; r < Rp; ++r) mbar_wait(&S.full[r % M2L_SYM_BUFS], (r / M2L_SYM_BUFS) & 1);
 }
 
 // column sums of the symmetric M2L: u(Y) += s * (Y's slots, in their fixed order).
