@@ -592,12 +592,12 @@ struct M2lGroupSmem {
     int abort;
 };
 
-// The symmetric form's block state: the same staging buffers (rounds of at most
-// M2L_SYM_CAP sources), each warp's column sums of the rounds in flight, a
-// per-warp transpose buffer for the column sums of one chunk, and per buffer
-// the round's first column slot, its sources and the warps done with it.
-// three staging buffers (one round of lookahead): with 1/r the block then fits
-// five times per SM (96 registers per thread, 43 KB of shared memory)
+// The symmetric form's block state: staging buffers like k_m2l_group's (rounds of
+// at most M2L_SYM_CAP sources), each warp's column sums of the rounds in flight,
+// a per-warp transpose buffer for the column sums of one chunk, and per buffer
+// the round's first column slot, its sources and the warps done with it. Three
+// staging buffers (one round of lookahead): with 1/r the block then fits five
+// times per SM (96 registers per thread, 43 KB of shared memory).
 constexpr int M2L_SYM_BUFS = 3;
 constexpr int M2L_SYM_AHEAD = M2L_SYM_BUFS - 2;
 constexpr int M2L_SYM_COLBUF = 32 * (2 * M2L_FOLD + 1);   // float2 per warp: L rows of 2 M2L_FOLD G + 1, L G <= 32
