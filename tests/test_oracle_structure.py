@@ -181,12 +181,17 @@ def test_figure1_golden(orc):
 @pytest.mark.parametrize("d,n,nu", [(2, 2000, 12), (3, 2500, 16)])
 def test_lists_symmetric_and_partition(orc, d, n, nu):
     """Y in IL(X) iff X in IL(Y); every leaf pair is covered exactly once,
-    by N at the leaf level or by IL at exactly one ancestor level."""
+    by N at the leaf level or by IL at exactly one ancestor level. Also what the
+    symmetric FP32 M2L relies on when it serves each pair {X, Y} from one side:
+    no cell has a sibling in its IL, and the parent of every Y in IL(X) is in
+    N(parent(X)) (Table 1)."""
     P = W.gaussian_mixture(n, d, 21, k=4, sigma=0.15)
     h = orc.H2(P, orc.Config(d=d, leaf_size=nu), structure_only=True)
     for c in range(h.ncell):
         for Y in h.il(c):
             assert c in set(h.il(Y).tolist())
+            assert h.cpar[Y] != h.cpar[c]
+            assert h.cpar[Y] in set(h.nb(h.cpar[c]).tolist())
         for Y in h.nb(c):
             assert c in set(h.nb(Y).tolist())
     leaves = list(h.level_cells(h.kappa))
