@@ -114,7 +114,11 @@ long orc_leaf_pivots(const orc_h2 *h, long cell, long *prow, long *pcol, long ca
 /* Form the stored H^2 representation (coupling S_{X,Y} and near blocks). */
 int orc_assemble(orc_h2 *h);
 
-/* H^2 product y = A~ x. form 0: on-the-fly kernel evaluation, form 1: stored. */
+/* H^2 product y = A~ x. form 0: on-the-fly kernel evaluation, form 1: stored,
+ * form 2: on the fly with the transverse pass (Sec. 4 step 3) taken over each
+ * unordered pair {X, Y}, Y in IL(X), once: S_{X,Y} = K(t^X, t^Y) is evaluated
+ * and applied as u^X += S w^Y and u^Y += S^T w^X (the kernel is symmetric and
+ * Y in IL(X) iff X in IL(Y)); serial, in cell order. */
 int orc_h2_matvec(const orc_h2 *h, const double *x, double *y, long nrhs, long ld, int form, int nthreads);
 /* Dense product y = A x in original order (Eq. 19 evaluated exactly). */
 void orc_dense_matvec(const orc_config *cfg, const double *P, long n, const double *x, double *y,

@@ -216,7 +216,8 @@ class H2:
         lib().orc_assemble(self._h)
 
     def matvec(self, x: np.ndarray, form: int = 0, nthreads: int = 0) -> np.ndarray:
-        """y = A~ x for x of shape (n,) or (nrhs, n); form 0 on the fly, 1 stored."""
+        """y = A~ x for x of shape (n,) or (nrhs, n); form 0 on the fly, 1 stored, 2 on the fly
+        with each admissible pair of cells evaluated once (S and its transpose)."""
         x = np.ascontiguousarray(x, dtype=np.float64)
         one = x.ndim == 1
         xx = x.reshape(1, -1) if one else x

@@ -82,7 +82,7 @@ int orc_h2_matvec(const orc_h2 *h, const double *x, double *y, long nrhs, long l
     /* nthreads > 0: that many threads; each output is summed by one thread in a
      * fixed order, so the result does not depend on it */
     const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
-    if (form == 1 && !h->s_blk) return -1;
+    if (form < 0 || form > 2 || (form == 1 && !h->s_blk)) return -1;
     const long n = h->n, nc = h->ncell, npiv = h->piv_off[nc];
     double *xs = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double *ys = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
@@ -120,8 +120,32 @@ int orc_h2_matvec(const orc_h2 *h, const double *x, double *y, long nrhs, long l
             }
         }
         /* step 3: transverse pass */
+        const long x0 = h->level_base[h->lmin <= h->kappa ? h->lmin : h->kappa + 1];
+        if (form == 2) {
+            /* each admissible pair once: S w^Y into u^X, S^T w^X into u^Y */
+            for (long X = x0; X < nc; ++X) {
+                const long *tX = h->piv_row + h->piv_off[X];
+                const long rX = h->piv_off[X + 1] - h->piv_off[X];
+                const double *wX = w + h->piv_off[X];
+                double *uX = u + h->piv_off[X];
+                for (long q = h->il_off[X]; q < h->il_off[X + 1]; ++q) {
+                    const long Y = h->il_idx[q];
+                    if (Y <= X) continue;
+                    const long *tY = h->piv_row + h->piv_off[Y];
+                    const long rY = h->piv_off[Y + 1] - h->piv_off[Y];
+                    const double *wY = w + h->piv_off[Y];
+                    double *uY = u + h->piv_off[Y];
+                    for (long a = 0; a < rX; ++a)
+                        for (long b = 0; b < rY; ++b) {
+                            const double k = orc_entry(h, tX[a], tY[b]);
+                            uX[a] = uX[a] + k * wY[b];
+                            uY[b] = uY[b] + k * wX[a];
+                        }
+                }
+            }
+        } else {
         #pragma omp parallel for num_threads(nt) schedule(dynamic, 16)
-        for (long X = h->level_base[h->lmin <= h->kappa ? h->lmin : h->kappa + 1]; X < nc; ++X) {
+        for (long X = x0; X < nc; ++X) {
             const long *tX = h->piv_row + h->piv_off[X];
             const long rX = h->piv_off[X + 1] - h->piv_off[X];
             double *uX = u + h->piv_off[X];
@@ -140,6 +164,7 @@ int orc_h2_matvec(const orc_h2 *h, const double *x, double *y, long nrhs, long l
                 }
                 uX[a] = s;
             }
+        }
         }
         /* step 4: downward pass, levels top-down, then leaves */
         for (int l = h->lmin + 1; l <= h->kappa; ++l) {

@@ -118,6 +118,24 @@ def test_stored_equals_on_the_fly(orc):
     assert np.array_equal(h.matvec(x, form=0), h.matvec(x, form=1))
 
 
+@pytest.mark.parametrize("wl,n,nu", [("invr3d_1m", 6000, 32), ("log2d_4096", 4096, 32), ("gauss_mix_256k", 4000, 32)])
+def test_symmetric_transverse_pass(orc, wl, n, nu):
+    """The transverse pass taken over each admissible pair of cells once (S applied to one
+    side, its transpose to the other; what the FP32 product's symmetric M2L computes) gives
+    the product of the per-cell pass within FP64 rounding, and both stay within the ACA
+    bound of the dense product (interaction lists are non-empty, so a pair the symmetric
+    pass missed would show as a far-field error far above 1e-13)."""
+    w = W.WORKLOADS[wl].scaled(n)
+    P = w.make_points()
+    h = orc.H2(P, cfg_for(orc, w, leaf_size=nu))
+    assert int(h.il_off[-1]) > 0
+    x = W.vector_normal(n, 5)
+    y0, y2 = h.matvec(x, form=0), h.matvec(x, form=2)
+    assert rel(y2, y0) < 1e-13
+    yd = orc.dense_matvec(P, x, cfg_for(orc, w, leaf_size=nu))
+    assert rel(y2, yd) < 10 * w.aca_tol + 1e-12
+
+
 def test_input_permutation(orc):
     """Points with distinct keys sort the same way whatever their input order, so
     the product of the permuted problem is the permuted product, bit for bit."""
