@@ -79,7 +79,8 @@ typedef struct {
     long *piv_off;                 /* [ncell+1] CSR of incoming pivots            */
     long *piv_row;                 /* t^{B,i}: sorted point positions             */
     long *piv_col;                 /* s^{B,i}: sorted point positions (-1 if pass-through) */
-    int *passthru;                 /* [ncell] 1 if the cell had no far-field candidates */
+    int *passthru;                 /* [ncell] 1 if the cell passed all candidates up (no far-field
+                                      candidates, or an ACA that used up every column) */
     long *cand_off;                /* [ncell+1] CSR of candidate rows t~^{B,i}    */
     long *cand;                    /* t~^{B,i}: sorted point positions            */
     long *op_off;                  /* [ncell+1] offsets into op                   */

@@ -31,10 +31,15 @@
  *    pivots in selection order. Leaf sets: sorted point order.
  *  - Levels above the first level with a non-empty interaction list need no
  *    pivots (nothing there takes part in a far-field interaction).
- *  - A cell whose far-field candidate set s~ is empty (its interaction list
- *    is empty, or holds only rank-0 cells) passes all its candidates up:
- *    t^{B,i} := t~^{B,i}, s^{B,i} := {} and its basis is the identity, so its
- *    points still reach the far field of its ancestors.
+ *  - A cell whose far-field candidate columns cannot determine its basis
+ *    passes all its candidates up: t^{B,i} := t~^{B,i}, s^{B,i} := {} and its
+ *    basis is the identity, so its points still reach the far field of its
+ *    ancestors. That is the case when s~ is empty (the interaction list is
+ *    empty or holds only rank-0 cells), and more generally when the ACA of
+ *    Sec. 2.2.1 uses up every column of s~ without meeting its stopping rule
+ *    while rows of t~ remain (rank = |s~| < |t~|): the cross then interpolates
+ *    A_{t~ s~} exactly but says nothing about the rows it did not pick, which
+ *    the ancestors' far field needs. The empty set is the case |s~| = 0.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -56,6 +61,17 @@ typedef struct {
     double *op;      /* m x r                */
     int passthru;
 } cell_out;
+
+/* all m candidate rows become the pivots t^{B,i}, with the identity basis */
+static void pass_through(cell_out *o, const long *rows, long m) {
+    o->passthru = 1;
+    o->r = m;
+    o->prow = (long *)malloc(sizeof(long) * (size_t)(m > 0 ? m : 1));
+    memcpy(o->prow, rows, sizeof(long) * (size_t)m);
+    o->pcol = NULL;
+    o->op = (double *)calloc((size_t)(m * m > 0 ? m * m : 1), sizeof(double));
+    for (long t = 0; t < m; ++t) o->op[t * m + t] = 1.0;
+}
 
 static void build_cell(const orc_h2 *h, long B, int leaf, cell_out *outs, cell_out *o) {
     const double eps = h->cfg.aca_tol;
@@ -98,13 +114,7 @@ static void build_cell(const orc_h2 *h, long B, int leaf, cell_out *outs, cell_o
     o->cand = rows;
     if (n == 0) {
         /* no far-field candidates: pass everything up, identity basis */
-        o->passthru = 1;
-        o->r = m;
-        o->prow = (long *)malloc(sizeof(long) * (size_t)(m > 0 ? m : 1));
-        memcpy(o->prow, rows, sizeof(long) * (size_t)m);
-        o->pcol = NULL;
-        o->op = (double *)calloc((size_t)(m * m > 0 ? m * m : 1), sizeof(double));
-        for (long t = 0; t < m; ++t) o->op[t * m + t] = 1.0;
+        pass_through(o, rows, m);
         free(cols);
         return;
     }
@@ -114,6 +124,12 @@ static void build_cell(const orc_h2 *h, long B, int leaf, cell_out *outs, cell_o
     long *pc = (long *)malloc(sizeof(long) * (size_t)(kmax > 0 ? kmax : 1));
     block_ctx ctx = {h, rows, cols};
     long r = orc_aca(m, n, block_entry, &ctx, eps, pr, pc, NULL, NULL);
+    if (r == n && r < m) {
+        /* every far-field column used, rows left: the basis is not determined */
+        free(pr); free(pc); free(cols);
+        pass_through(o, rows, m);
+        return;
+    }
     o->passthru = 0;
     o->r = r;
     o->prow = (long *)malloc(sizeof(long) * (size_t)(r > 0 ? r : 1));

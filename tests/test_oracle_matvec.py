@@ -216,3 +216,105 @@ def test_passes_match_assembled_matrix(orc, wl, n, nu):
     x = W.vector_normal(n, 8)
     ys = h.matvec(x)[h.perm]          # product in tree order
     assert rel(ys, M @ x[h.perm]) < 1e-13
+
+
+# --- pass-through cells -------------------------------------------------------
+# A cell whose far-field candidate columns cannot determine its basis (no
+# candidates at all, or an ACA that used up every candidate column without
+# meeting its stopping rule while candidate rows remain) passes all its
+# candidate rows up with the identity basis, so that its points still reach
+# the far field of its ancestors. These clouds contain such cells; the pins are
+# the dense product, for a full vector and for a vector supported only on the
+# points of pass-through cells, whose far field would vanish if those points
+# were dropped.
+
+def background_and_cluster(n_background, n_cluster, delta, seed):
+    """Sparse uniform points in [0,1]^3 plus one tight Gaussian cluster: the uniform
+    tree goes deep for the cluster, and the background points' cells form chains of
+    cells with tiny or empty interaction-list regions."""
+    rng = np.random.default_rng(seed)
+    centre = np.array([0.3, 0.6, 0.45])
+    return np.vstack([rng.uniform(0.0, 1.0, (n_background, 3)),
+                      centre + delta * rng.standard_normal((n_cluster, 3))])
+
+
+def far_field_columns(h, c):
+    """|s~| of cell c: points of the IL cells (leaf) or their children's pivots."""
+    if h.level_of(c) == h.kappa:
+        return int(sum(h.cend[Y] - h.cbeg[Y] for Y in h.il(c)))
+    return int(sum(h.piv_off[z + 1] - h.piv_off[z] for Y in h.il(c) for z in range(h.cch_beg[Y], h.cch_end[Y])))
+
+
+def near_only(h, x_sorted):
+    """The leaf-level near field alone (Sec. 3 step 3), in sorted order."""
+    y = np.zeros(h.n)
+    for c in h.level_cells(h.kappa):
+        cols = np.concatenate([np.arange(h.cbeg[Y], h.cend[Y]) for Y in h.nb(c)])
+        rows = np.arange(h.cbeg[c], h.cend[c])
+        y[rows] = orc_entry(h, rows, cols) @ x_sorted[cols]
+    return y
+
+
+def orc_entry(h, rows, cols):
+    from oracle import oracle as O
+    return O.entry_block(h, rows, cols)
+
+
+PASSTHRU_CASES = [
+    # name, points, leaf size, kernel, kparam
+    ("gauss_mix_8000", lambda: W.WORKLOADS["gauss_mix_256k"].scaled(8000).make_points(), 16, W.K_GAUSS,
+     (1.0, 0.2, 1.0, 0.0)),
+    ("cluster_540", lambda: background_and_cluster(500, 40, 1e-4, 2), 8, W.K_INV_R, (1.0, 0.0, 0.0, 0.0)),
+    ("coincident_250", lambda: np.repeat(W.uniform_cube(50, 3, 3), 5, axis=0), 3, W.K_INV_R, (1.0, 0.0, 0.0, 0.0)),
+]
+
+
+@pytest.mark.parametrize("name,make,nu,kernel,kparam", PASSTHRU_CASES, ids=[c[0] for c in PASSTHRU_CASES])
+def test_passthrough_against_dense(orc, name, make, nu, kernel, kparam):
+    P = make()
+    n = P.shape[0]
+    eps = 1e-8
+    cfg = orc.Config(d=3, leaf_size=nu, aca_tol=eps, kernel=kernel, kparam=kparam)
+    h = orc.H2(P, cfg)
+    pt = np.nonzero(h.passthru)[0]
+    assert len(pt) > 0
+    for c in pt:
+        # all candidates passed up, with the identity basis and no column pivots
+        m = int(h.cand_off[c + 1] - h.cand_off[c])
+        assert h.piv_off[c + 1] - h.piv_off[c] == m
+        assert np.array_equal(h.pivots(c), h.candidates(c))
+        assert np.array_equal(h.operator(c), np.eye(m))
+        assert np.all(h.colpivots(c) == -1)
+    if name != "gauss_mix_8000":
+        # pass-through above the leaves, and cells whose ACA used up its columns
+        assert any(h.level_of(c) < h.kappa for c in pt)
+        assert any(far_field_columns(h, c) > 0 for c in pt)
+    x = W.vector_normal(n, 5)
+    assert rel(h.matvec(x), orc.dense_matvec(P, x, cfg)) <= 10 * eps
+    # a vector on the points of pass-through cells only
+    on = np.zeros(n, dtype=bool)
+    for c in pt:
+        on[h.perm[h.cbeg[c]:h.cend[c]]] = True
+    xs = np.where(on, x, 0.0)
+    yd = orc.dense_matvec(P, xs, cfg)
+    assert rel(h.matvec(xs), yd) <= 10 * eps
+    # the far field carries much of that product: dropping those points from it
+    # would miss the dense product by far more than the bound above
+    yn = np.empty(n)
+    yn[h.perm] = near_only(h, xs[h.perm])
+    assert rel(yn, yd) > 1e-2
+
+
+def test_passthrough_assembled_matrix(orc):
+    """On a cloud with pass-through chains the passes reproduce the H^2 matrix written
+    out from its nested bases (identity blocks for pass-through cells), and that matrix
+    is within the ACA bound of A."""
+    P = background_and_cluster(300, 30, 1e-4, 4)
+    cfg = orc.Config(d=3, leaf_size=8, aca_tol=1e-8, kernel=W.K_INV_R, kparam=(1.0, 0, 0, 0))
+    h = orc.H2(P, cfg)
+    assert h.passthru.sum() > 0 and h.lmin < h.kappa
+    M = assembled_matrix(orc, h, cfg)
+    A = orc.entry_block(h, range(h.n), range(h.n))
+    assert rel(M, A) < 100 * cfg.aca_tol
+    x = W.vector_normal(h.n, 8)
+    assert rel(h.matvec(x)[h.perm], M @ x[h.perm]) < 1e-13
