@@ -116,7 +116,7 @@ typedef struct {
     int64_t n_il, n_nb;            /* interaction-list and neighbour entries       */
     int64_t n_pivots;              /* sum of ranks over all cells                  */
     int64_t max_rank;
-    int64_t n_passthru;            /* cells with no far-field candidates           */
+    int64_t n_passthru;            /* pass-through cells (all candidates kept)     */
     int64_t p2p_pairs;             /* sum over leaves of n_B * sum_{N(B)} n_B'     */
     int64_t m2l_pairs;             /* sum over cells of r_B * sum_{IL(B)} r_B'     */
     int64_t op_entries;            /* entries of all bases and translations        */
@@ -201,6 +201,21 @@ nnca_status nnca_matvec_noalloc(nnca_handle h, const void *x, void *y, int64_t l
 nnca_status nnca_matvec_batch(const nnca_handle *h, int count, const void *const *x, void *const *y,
                               const int64_t *ld, int64_t nrhs, int dtype, int precision, void *stream);
 
+/* Testing hook for the bounded waits of the FP32 product (the paper has no
+ * counterpart; a failure-handling service). The FP32 M2L and near-field kernels
+ * wait on shared-memory barriers of their own thread block for their own bulk
+ * copies; a wait that runs out of its clock budget sets bit 16 of
+ * nnca_stats.device_status, lets the block's copies in flight land and returns,
+ * so the context stays usable and the product is reported invalid.
+ *   wait_limit_clocks > 0 sets the budget of one wait (<= 0: the default, 2^31);
+ *   extra_tx_bytes > 0 adds that many bytes to every staging round's expected
+ *     byte count, more than its copies deliver, so that every wait on a round
+ *     runs out although every copy lands (0: normal operation).
+ * Applies on the current device to every product launched after the call;
+ * synchronises the device. Products run with extra_tx_bytes > 0 are invalid:
+ * restore (0, 0) before further use. */
+nnca_status nnca_set_wait_test(int64_t wait_limit_clocks, unsigned extra_tx_bytes);
+
 /* Free every device and host resource of the handle (NULL is a no-op).
  * Synchronises the device first. */
 void nnca_destroy(nnca_handle h);
@@ -230,7 +245,9 @@ nnca_status nnca_set_profiling(nnca_handle h, int on);
  *   PIV_OFF     int64[ncell+1]  CSR offsets of the pivots (ranks)
  *   PIV_ROW     int64[npiv]     t^{B,i} (sorted positions)
  *   PIV_COL     int64[npiv]     s^{B,i} (sorted positions; -1 for pass-through cells)
- *   PASSTHRU    int64[ncell]    1 if the cell had no far-field candidates
+ *   PASSTHRU    int64[ncell]    1 if the cell passed all its candidates up (no
+ *                               far-field candidates, or an ACA that used up
+ *                               every candidate column with rows left)
  *   CAND_OFF    int64[ncell+1]  CSR offsets of the candidate rows t~^{B,i}
  *   OP_OFF      int64[ncell+1]  offsets of the per-cell operators
  *   OP          double[...]     per cell |t~| x r row-major: U_B (leaf) or

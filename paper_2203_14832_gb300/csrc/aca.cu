@@ -17,8 +17,11 @@
 //     by LU with partial pivoting of (A_{tau sigma})^T and one forward and
 //     back substitution per candidate row; rows of X at the pivots are the
 //     identity by definition and are set exactly.
-// A cell with no far-field candidates passes all its candidates up with an
-// identity basis. The ACA reading (start row, tie breaks, the cross that meets
+// A cell whose far-field candidates cannot determine its basis passes all its
+// candidates up with an identity basis: no candidates at all, or an ACA that
+// used up every candidate column without meeting its stopping rule while rows
+// remain (rank = |s~| < |t~|: the cross says nothing about the rows it did not
+// pick, which the ancestors' far field needs). The ACA reading (start row, tie breaks, the cross that meets
 // the stopping rule is not kept) is the one stated in the library header.
 //
 // ACA scratch (the residual row, the crosses u_l and v_l) comes from one pool
@@ -124,6 +127,7 @@ struct AcaArgs {
     const int64_t *row_off, *col_off, *cap_off;
     const int32_t *rows, *cols;
     int32_t *rank, *prow, *pcol;  // outputs (local indices; capacity cap per cell)
+    int32_t *pass;                // output: 1 for a pass-through cell
     const int32_t *work;
     int nwork;
     int *work_ctr;
@@ -207,7 +211,10 @@ __global__ void __launch_bounds__(ACA_T) k_aca(AcaArgs A) {
             // no far-field candidates: pass-through (all rows), or an empty cell
             if (n == 0)
                 for (int64_t i = t; i < m; i += ACA_T) { prow[i] = (int32_t)i; pcol[i] = -1; }
-            if (t == 0) A.rank[x] = (n == 0) ? (int32_t)m : 0;
+            if (t == 0) {
+                A.rank[x] = (n == 0) ? (int32_t)m : 0;
+                A.pass[x] = (n == 0) ? 1 : 0;
+            }
             continue;
         }
         const int64_t kmax = m < n ? m : n;
@@ -390,7 +397,16 @@ __global__ void __launch_bounds__(ACA_T) k_aca(AcaArgs A) {
             i = bi;
         }
         __syncthreads();
-        if (s_ctl != 2 && t == 0) A.rank[x] = (int32_t)k;
+        if (s_ctl != 2) {
+            // every column used without meeting the stopping rule, rows left: pass-through
+            const bool pass = k == n && k < m;
+            if (pass)
+                for (int64_t q = t; q < m; q += ACA_T) { prow[q] = (int32_t)q; pcol[q] = -1; }
+            if (t == 0) {
+                A.rank[x] = pass ? (int32_t)m : (int32_t)k;
+                A.pass[x] = pass ? 1 : 0;
+            }
+        }
         __syncthreads();
     }
 }
@@ -539,8 +555,9 @@ __global__ void k_sizes_prod(int64_t cnt, const int64_t *a_off, const int32_t *r
 __global__ void k_cap_sizes(int64_t cnt, const int64_t *msz, const int64_t *nsz, int64_t *cap, int32_t *pass) {
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < cnt; x += (int64_t)gridDim.x * blockDim.x) {
         const int64_t m = msz[x], n = nsz[x];
-        cap[x] = n == 0 ? m : (m < n ? m : n);
-        pass[x] = n == 0 ? 1 : 0;
+        (void)n;
+        cap[x] = m;        // a pass-through cell keeps all m candidate rows
+        pass[x] = 0;       // set by the ACA
     }
 }
 
@@ -657,6 +674,7 @@ void build_pivots_impl(Handle *h, std::vector<LevelOut> &lv, Scratch &keep) {
             A.rank = L.rank;
             A.prow = prow_cap;
             A.pcol = pcol_cap;
+            A.pass = L.pass;
             A.work = work;
             A.nwork = nwork;
             A.work_ctr = ctrs;

@@ -82,8 +82,10 @@ def test_full_parity(gpu, orc, wl, n, kw, tol32):
         assert np.array_equal(op, o.op)
     else:
         # CUDA's log/exp and the host's may differ in the last place; the solve
-        # with the pivot block A_{tau sigma} (condition ~ 1/eps) amplifies that
-        assert np.max(np.abs(op - o.op)) <= 1e-5 * max(1.0, np.max(np.abs(o.op)))
+        # with the pivot block A_{tau sigma} amplifies that. Measured on GB300:
+        # 2.5e-9 (log r, 4096 points), 1.0e-10 (Gaussian, 15,000 points) of
+        # max(1, max |X|); the bound keeps a margin of 4x over the larger
+        assert np.max(np.abs(op - o.op)) <= 1e-8 * max(1.0, np.max(np.abs(o.op)))
     x = w.make_vector() if w.nrhs == 1 else w.make_vector()[:2]
     yo = o.matvec(x)
     xd = torch.as_tensor(np.ascontiguousarray(x), device="cuda")
@@ -158,7 +160,10 @@ def test_dimensions(gpu, orc, d, n, nu):
     yo = o.matvec(x)
     xd = torch.as_tensor(x, device="cuda")
     y = g.matvec(xd).cpu().numpy()
-    assert rel(y, yo) < 1e-12
+    # the 1D log r representation has basis entries up to 2.7e4 (ill-conditioned
+    # pivot blocks; the bases also differ from the host's in the last place of log),
+    # which amplifies the different rounding orders of the two products
+    assert rel(y, yo) < (1e-10 if d == 1 else 1e-12)
     g.close()
 
 
@@ -266,34 +271,110 @@ def test_invalid_arguments(gpu):
 
 @pytest.mark.slow
 def test_full_size_invr3d(gpu, orc):
-    """The 1,048,576-point 1/r workload in the configuration the benchmark times:
-    structure bit-exact against the oracle, sampled leaf pivots bit-exact,
-    FP32 against FP64 within 1e-6, FP64 against dense rows within 10 eps,
-    and the symmetry of the product."""
+    """The 1,048,576-point 1/r workload in the configuration the benchmark times,
+    against the oracle's own full-size H^2: structure, every pivot and every basis
+    entry bit-exact; the FP64 product within 1e-12 and the FP32 product within 1e-6
+    of the oracle's H^2 product; FP32 within 1e-6 of FP64; FP64 within 10 eps of the
+    dense product on 4096 sampled rows; and the symmetry of the product."""
+    import os
     import torch
     w = W.WORKLOADS["invr3d_1m"]
     P = w.make_points()
     gcfg, ocfg = configs(gpu, orc, w)
     g = gpu.H2(torch.as_tensor(P, device="cuda"), gcfg)
-    o = orc.H2(P, ocfg, structure_only=True)
+    threads = len(os.sched_getaffinity(0))
+    o = orc.H2(P, ocfg, nthreads=threads)
     check_structure(g, o)
-    poff, prow, pcol = g.export("PIV_OFF"), g.export("PIV_ROW"), g.export("PIV_COL")
-    rng = np.random.default_rng(0)
-    for c in rng.choice(np.arange(o.level_base[o.kappa], o.level_base[o.kappa + 1]), 24, replace=False):
-        r_o, c_o = o.leaf_pivots(int(c))
-        assert np.array_equal(prow[poff[c]:poff[c + 1]], r_o)
-        assert np.array_equal(pcol[poff[c]:poff[c + 1]], c_o)
+    check_pivots(g, o)
+    assert np.array_equal(g.export("OP"), o.op)
     x = w.make_vector()
     xd = torch.as_tensor(x, device="cuda")
     y64 = g.matvec(xd, gpu.PREC_FP64).cpu().numpy()
     y32 = g.matvec(xd, gpu.PREC_FP32).cpu().numpy()
+    yo = o.matvec(x, nthreads=threads)
+    assert rel(y64, yo) <= 1e-12
+    assert rel(y32, yo) <= 1e-6
     assert rel(y32, y64) <= 1e-6
-    rows = rng.choice(w.n, 256, replace=False)
-    yd = orc.dense_rows(P, rows, x, ocfg)
+    rng = np.random.default_rng(0)
+    rows = rng.choice(w.n, 4096, replace=False)
+    yd = orc.dense_rows(P, rows, x, ocfg, nthreads=threads)
     assert rel(y64[rows], yd) <= 10 * w.aca_tol
     z = W.vector_normal(w.n, 77)
     az = g.matvec(torch.as_tensor(z, device="cuda")).cpu().numpy()
     assert abs(x @ az - z @ y64) <= 1e-12 * np.linalg.norm(x) * np.linalg.norm(az)
+    assert g.stats()["device_status"] & (2 | 16) == 0
+    g.close()
+
+
+def background_and_cluster(n_background, n_cluster, delta, seed):
+    rng = np.random.default_rng(seed)
+    centre = np.array([0.3, 0.6, 0.45])
+    return np.vstack([rng.uniform(0.0, 1.0, (n_background, 3)),
+                      centre + delta * rng.standard_normal((n_cluster, 3))])
+
+
+PT_CLOUDS = [
+    # name, points, leaf size: pass-through chains (empty candidate sets and ACAs
+    # that used up their columns), coincident points below nu and above 96 per leaf
+    ("cluster_2040", lambda: background_and_cluster(2000, 40, 1e-4, 2), 8),
+    ("coincident_250", lambda: np.repeat(W.uniform_cube(50, 3, 3), 5, axis=0), 3),
+    ("coincident_1800", lambda: np.repeat(W.uniform_cube(12, 3, 7), 150, axis=0), 64),
+]
+
+
+@pytest.mark.parametrize("name,make,nu", PT_CLOUDS, ids=[c[0] for c in PT_CLOUDS])
+def test_passthrough_clouds(gpu, orc, name, make, nu):
+    """Clouds with pass-through cells at many levels: structure, pivots and pass-through
+    flags bit-exact; FP64 within 1e-12 and FP32 (one and four right-hand sides; leaves of
+    150 coincident points take the FP32 ring kernel) within 1e-6 of the oracle's H^2."""
+    import torch
+    P = make()
+    n = P.shape[0]
+    kw = dict(d=3, leaf_size=nu, aca_tol=1e-8, kernel=W.K_INV_R, kparam=(1.0, 0.0, 0.0, 0.0))
+    g = gpu.H2(torch.as_tensor(P, device="cuda"), gpu.Config(**kw))
+    o = orc.H2(P, orc.Config(**kw))
+    check_structure(g, o)
+    check_pivots(g, o)
+    assert o.passthru.sum() > 0
+    assert np.array_equal(g.export("OP"), o.op)
+    X = W.vector_normal(n, 11, nrhs=4)
+    yo = [o.matvec(X[r].copy()) for r in range(4)]
+    y64 = g.matvec(torch.as_tensor(X[0].copy(), device="cuda"), gpu.PREC_FP64).cpu().numpy()
+    assert rel(y64, yo[0]) < 1e-12
+    y32 = g.matvec(torch.as_tensor(X[0].copy(), device="cuda"), gpu.PREC_FP32).cpu().numpy()
+    assert rel(y32, yo[0]) < 1e-6
+    Y32 = g.matvec(torch.as_tensor(X, device="cuda"), gpu.PREC_FP32).cpu().numpy()
+    for r in range(4):
+        assert rel(Y32[r], yo[r]) < 1e-6
+    assert g.stats()["device_status"] & (2 | 16) == 0
+    g.close()
+
+
+@pytest.mark.parametrize("kernel,kparam", [(W.K_INV_R, (1.0, 0.0, 0.0, 0.0)), (W.K_GAUSS, (1.0, 0.2, 1.0, 0.0))])
+def test_fp32_large_leaves(gpu, orc, kernel, kparam):
+    """Leaf size 128 on 44,000 uniform points (leaves of up to about 110 points): leaves
+    above 96 points take the FP32 ring kernel (k_leaf_f32) for one right-hand side, and
+    the per-right-hand-side near field in passes of four; 1/r and the Gaussian kernel;
+    every column within 1e-6 of the oracle's H^2 product."""
+    import torch
+    n = 44000
+    w = W.WORKLOADS["invr3d_1m"].scaled(n)
+    P = w.make_points()
+    gcfg, ocfg = configs(gpu, orc, w, leaf_size=128, kernel=kernel, kparam=kparam)
+    g = gpu.H2(torch.as_tensor(P, device="cuda"), gcfg)
+    o = orc.H2(P, ocfg)
+    check_pivots(g, o)
+    cb, ce = g.export("CBEG"), g.export("CEND")
+    lb = g.export("LEVEL_BASE")
+    assert np.max((ce - cb)[lb[-2]:lb[-1]]) > 96
+    X = W.vector_normal(n, 41, nrhs=4)
+    yo = [o.matvec(X[r].copy()) for r in range(4)]
+    y1 = g.matvec(torch.as_tensor(X[0].copy(), device="cuda"), gpu.PREC_FP32).cpu().numpy()
+    assert rel(y1, yo[0]) < 1e-6
+    Y32 = g.matvec(torch.as_tensor(X, device="cuda"), gpu.PREC_FP32).cpu().numpy()
+    for r in range(4):
+        assert rel(Y32[r], yo[r]) < 1e-6
+    assert g.stats()["device_status"] & (2 | 16) == 0
     g.close()
 
 
