@@ -41,6 +41,16 @@ unsigned read_status(Handle *h) {
     return v;
 }
 
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a{};
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 void prof_mark(Handle *h, int slot) {
     (void)slot;
     if (!h->profile) return;
@@ -75,16 +85,6 @@ void prof_flush(Handle *h) {
     }
     for (cudaEvent_t e : h->prof_events) h->event_pool.push_back(e);
     h->prof_events.clear();
-}
-
-bool is_device_ptr(const void *p) {
-    cudaPointerAttributes a{};
-    cudaError_t e = cudaPointerGetAttributes(&a, p);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
 nnca_status fail(Handle *h, nnca_status s, const std::string &msg) {
@@ -357,6 +357,15 @@ nnca_status nnca_matvec_host(nnca_handle h, const void *x_host, void *y_host, in
         return fail(h, e.status, e.what());
     } catch (const std::exception &e) {
         return fail(h, NNCA_ERR_INTERNAL, e.what());
+    }
+    return NNCA_OK;
+}
+
+nnca_status nnca_set_wait_test(int64_t wait_limit_clocks, unsigned extra_tx_bytes) {
+    try {
+        set_wait_test(wait_limit_clocks, extra_tx_bytes);
+    } catch (const Error &e) {
+        return fail(nullptr, e.status, e.what());
     }
     return NNCA_OK;
 }

@@ -636,9 +636,18 @@ __device__ __forceinline__ void mbar_arrive(void *bar) {
 __device__ __forceinline__ void mbar_arrive_tx(void *bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
-// wait until the phase of the given parity has completed; false after about 2^31 clocks
+// The bounded waits' clock budget and the bytes added to every staging round's
+// expected transaction count, in device memory so that a test can change them
+// (nnca_set_wait_test): 2^31 clocks and 0 in normal use. With extra bytes the
+// rounds' phases never complete although every copy lands, so every wait on
+// them runs out.
+__device__ long long g_wait_limit = 1ll << 31;
+__device__ unsigned g_stage_extra_tx = 0u;
+
+// wait until the phase of the given parity has completed; false after g_wait_limit clocks
 __device__ __forceinline__ bool mbar_wait(void *bar, unsigned parity) {
     const unsigned a = smem_addr(bar);
+    const long long lim = g_wait_limit;
     const long long t0 = clock64();
     for (;;) {
         unsigned ok;
@@ -648,7 +657,7 @@ __device__ __forceinline__ bool mbar_wait(void *bar, unsigned parity) {
                      : "r"(a), "r"(parity)
                      : "memory");
         if (ok) return true;
-        if (clock64() - t0 > (1ll << 31)) return false;
+        if (clock64() - t0 > lim) return false;
     }
 }
 // the same wait taken by a whole warp: it succeeds only if it succeeds for every lane
@@ -725,7 +734,7 @@ __device__ __forceinline__ int m2l_stage(SM &S, int b, unsigned use, StageCursor
     if (lane == 0) S.nrec[b] = nrec;
     stage_note(S, b, total);
     __syncwarp();
-    if (lane == 0) mbar_arrive_tx(&S.full[b], total);
+    if (lane == 0) mbar_arrive_tx(&S.full[b], total + g_stage_extra_tx);
     __syncwarp();
     if (lane < nrec) bulk_g2s(&S.src[b][r.z & 0x7ff][0], spk + 2 * (int64_t)r.y, bytes, &S.full[b]);
     if (k + nrec < kend) stage_load(cur, plan, plan_sh, k + nrec, kend);
@@ -1135,7 +1144,7 @@ __device__ __forceinline__ int near_stage(NearWarpSmem &W, int b, const NearCurs
     // the buffer's previous contents were read by this warp's generic loads
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncwarp();
-    if (lane == 0) mbar_arrive_tx(&W.full[b], total);
+    if (lane == 0) mbar_arrive_tx(&W.full[b], total + g_stage_extra_tx);
     __syncwarp();
     if (lane < nrec) bulk_g2s(&W.u[b][c.r.z & 0x7ff], src, bytes, &W.full[b]);
     return k + nrec;
@@ -1743,7 +1752,7 @@ __device__ __forceinline__ int m2l_stage_rhs(M2lRhsSmem &S, int b, unsigned use,
     const unsigned total = __reduce_add_sync(0xffffffffu, bytes);
     if (lane == 0) S.nrec[b] = nrec;
     __syncwarp();
-    if (lane == 0) mbar_arrive_tx(&S.full[b], total);
+    if (lane == 0) mbar_arrive_tx(&S.full[b], total + g_stage_extra_tx);
     __syncwarp();
     if (lane < nrec) {
         bulk_g2s(&S.src[b][r.z & 0x7ff][0], spk + 2 * (int64_t)r.y, np * 32u, &S.full[b]);
@@ -2489,6 +2498,13 @@ void dispatch_kind(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld) 
 }
 
 }  // namespace
+
+void set_wait_test(int64_t wait_limit_clocks, unsigned extra_tx_bytes) {
+    const long long lim = wait_limit_clocks > 0 ? (long long)wait_limit_clocks : (1ll << 31);
+    NNCA_CUDA(cudaMemcpyToSymbol(g_wait_limit, &lim, sizeof(lim)));
+    NNCA_CUDA(cudaMemcpyToSymbol(g_stage_extra_tx, &extra_tx_bytes, sizeof(extra_tx_bytes)));
+    NNCA_CUDA(cudaDeviceSynchronize());
+}
 
 void matvec(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int dtype, int precision) {
     const bool radial = kernel_is_radial(h->kp.kind);

@@ -378,12 +378,16 @@ void build_lists(Handle *h);
 void build_pivots(Handle *h);   // pivots, bases, global pivot/operator arrays
 void build_finish(Handle *h);   // data of the product: centres, FP32 coordinates, work lists
 void matvec(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int dtype, int precision);
+// wait budget and extra expected bytes of the FP32 kernels' staging (nnca_set_wait_test)
+void set_wait_test(int64_t wait_limit_clocks, unsigned extra_tx_bytes);
 
 // Exclusive scan of n uint32/int64 values (scan.cu). out may alias in.
 void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s, Scratch &scr);
 int64_t scan_total_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s, Scratch &scr);
 
 unsigned read_status(Handle *h);
+// true for device (or managed) memory; false for host memory and unknown pointers
+bool is_device_ptr(const void *p);
 // Record the profiling event that ends pass `slot` (0 = start of the product).
 void prof_mark(Handle *h, int slot);
 

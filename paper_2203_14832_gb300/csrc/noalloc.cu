@@ -63,6 +63,10 @@ extern "C" nnca_status nnca_matvec_noalloc(nnca_handle hh, const void *x, void *
         h->last_error = "nnca_matvec_noalloc: invalid x, y, ld, dtype or precision";
         return NNCA_ERR_INVALID_ARG;
     }
+    if (!nnca::is_device_ptr(x) || !nnca::is_device_ptr(y)) {
+        h->last_error = "nnca_matvec_noalloc: x and y must be device memory";
+        return NNCA_ERR_INVALID_ARG;
+    }
     if (h->profile) {
         h->last_error = "nnca_matvec_noalloc: turn profiling off first (it creates events)";
         return NNCA_ERR_INVALID_ARG;

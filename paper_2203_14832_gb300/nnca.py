@@ -29,8 +29,9 @@ F64, F32 = 0, 1
 PREC_FP64, PREC_FP32 = 0, 1
 EXPORTS = ["PERM", "KEYS", "LEVEL_BASE", "CKEY", "CBEG", "CEND", "CPAR", "CCH_BEG", "CCH_END", "NB_OFF", "NB_IDX",
            "IL_OFF", "IL_IDX", "PIV_OFF", "PIV_ROW", "PIV_COL", "PASSTHRU", "CAND_OFF", "OP_OFF", "OP"]
-SYMBOLS = ["nnca_build", "nnca_matvec", "nnca_matvec_host", "nnca_matvec_noalloc", "nnca_destroy", "nnca_get_stats",
-           "nnca_export", "nnca_set_profiling", "nnca_last_error", "nnca_status_string"]
+SYMBOLS = ["nnca_build", "nnca_matvec", "nnca_matvec_host", "nnca_matvec_noalloc", "nnca_matvec_batch",
+           "nnca_destroy", "nnca_get_stats", "nnca_export", "nnca_set_profiling", "nnca_set_wait_test",
+           "nnca_last_error", "nnca_status_string"]
 
 
 class NncaError(RuntimeError):
@@ -83,6 +84,8 @@ def lib() -> C.CDLL:
         L.nnca_matvec_batch.restype = C.c_int
         L.nnca_matvec_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(C.c_int64),
                                         C.c_int64, C.c_int, C.c_int, vp]
+        L.nnca_set_wait_test.restype = C.c_int
+        L.nnca_set_wait_test.argtypes = [C.c_int64, C.c_uint]
         L.nnca_set_profiling.restype = C.c_int
         L.nnca_set_profiling.argtypes = [vp, C.c_int]
         L.nnca_last_error.restype = C.c_char_p
@@ -182,6 +185,12 @@ def nnca_matvec_host(handle, x: np.ndarray, y: np.ndarray, nrhs: int, ld: int, p
     assert x.dtype == y.dtype and x.flags.c_contiguous and y.flags.c_contiguous
     _check(lib().nnca_matvec_host(handle, x.ctypes.data, y.ctypes.data, nrhs, ld, dtype, precision,
                                   _stream_ptr(stream)), handle)
+
+
+def nnca_set_wait_test(wait_limit_clocks: int, extra_tx_bytes: int) -> None:
+    """Testing hook of the FP32 kernels' bounded waits (include/nnca.h); (0, 0)
+    restores normal operation."""
+    _check(lib().nnca_set_wait_test(int(wait_limit_clocks), int(extra_tx_bytes)), None)
 
 
 def nnca_destroy(handle) -> None:
