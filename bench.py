@@ -44,8 +44,9 @@ from paper_2203_14832_gb300 import workloads as W  # noqa: E402
 METRIC = "H2 matvec points/s at rel err <=1e-6: mixed-precision vs FP64 form, same GB300"
 WORKLOAD = "invr3d_1m"
 CPU_SAMPLE_N = 65536          # oracle sample: the same recipe at 65,536 points
-SMS = 152
 MUFU_PER_CLK_SM = 16          # MUFU lanes per SM per clock: one rsqrt per pair
+FP32_PER_CLK_SM = 128         # FP32 lanes per SM per clock
+NEAR_OPS_PER_PAIR = 13        # FP32 lane-ops per near-field pair (hi/lo differences, squares, rsqrt scale, fma)
 
 
 def parse():
@@ -343,7 +344,9 @@ def run_ours(args):
     pass_ms = [v / calls for v in st_prof["pass_ms"][:6]]
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_gpair = MUFU_PER_CLK_SM * SMS * sm_max * 1e6 / 1e9
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak_gpair = MUFU_PER_CLK_SM * sms * sm_max * 1e6 / 1e9
+    passes = pass_rooflines(h, st, pass_ms, sms, sm_max, peaks, nrhs if nrhs < 4 else 4)
     # kernel evaluations of the pass: each pivot pair once in the symmetric form
     # (a value serves the row and the column sum), else every ordered pair
     evals = st.get("m2l_evals") or st["m2l_pairs"]
@@ -382,13 +385,14 @@ def run_ours(args):
                     "l2p_p2p": pass_ms[4], "total": pass_ms[5]},
         "roofline": {"bound": "alu", "kernel": m2l_kernel, "achieved": achieved, "peak": peak_gpair,
                      "unit": "G kernel evaluations/s", "frac": achieved / peak_gpair, "traffic": traffic,
-                     "peak_note": f"one MUFU rsqrt per evaluation: {MUFU_PER_CLK_SM}/clk/SM x {SMS} SMs x "
+                     "peak_note": f"one MUFU rsqrt per evaluation: {MUFU_PER_CLK_SM}/clk/SM x {sms} SMs x "
                                   f"{sm_max:.0f} MHz",
                      "pairs_served_per_s_frac": st["m2l_pairs"] / (m2l_ms / 1e3) / 1e9 / peak_gpair,
                      "pairs_note": "symmetric form: each evaluation feeds two ordered pivot pairs (a row and "
                                    "a column sum); this fraction counts those pairs against the same peak",
                      "traffic_note": ("DRAM bytes read + written by one M2L launch: " + traffic_note) if traffic_note
                      else "no full-size ncu DRAM figure for this kernel and workload"},
+        "roofline_passes": passes,
         "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": N * nrhs * 8,
                 "d2h_bytes_per_step": N * nrhs * 8, "matches_device_result": e2e_ok},
         "gpu_launches": int(st_prof["launches_per_product"]) * args.steps,
@@ -401,6 +405,59 @@ def run_ours(args):
     if err32 > 1e-6 and WORKLOAD == "invr3d_1m":
         print(f"error gate failed: FP32 form {err32:.3e} > 1e-6 against FP64", file=sys.stderr)
         sys.exit(3)
+
+
+def pass_rooflines(h, st, pass_ms, sms, sm_mhz, peaks, nr):
+    """Achieved fraction of its roofline for every pass of one FP32 product (pass
+    times from CUDA events on the launching stream; nr right-hand sides per pass).
+
+    Algorithmic work per pass (counted exactly from the built representation):
+      M2L     kernel evaluations (m2l_evals), one MUFU rsqrt each
+      P2P+L2P point pairs (p2p_pairs), bound by the FP32 pipe at NEAR_OPS_PER_PAIR
+              lane-ops per pair (below the MUFU rate of one rsqrt per pair)
+      P2M+M2M operator bytes (FP64 bases of every cell, read once per pass) plus the
+              vector in tree order and the multipole coefficients, against HBM
+      L2L     FP64 translation operators of the non-leaf cells plus the local
+              coefficients (read and written), against HBM
+    The build's k_aca (FP64 ACA) is reported from its ncu capture, whose FP64-pipe
+    activity is the fraction."""
+    lb = h.export("LEVEL_BASE")
+    op_off = h.export("OP_OFF")
+    op_nonleaf = int(op_off[lb[st["kappa"]]])
+    op_all = int(st["op_entries"])
+    npiv, n = int(st["n_pivots"]), int(st["n"])
+    clk = sm_mhz * 1e6
+    hbm = float(peaks.get("hbm_gbs", 6800.0)) * 1e9
+    hbm_note = "measured copy bandwidth" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
+
+    def ent(name, kernels, bound, work, unit, ms, peak, note):
+        ach = work / (ms / 1e3) if ms > 0 else 0.0
+        return {"pass": name, "kernels": kernels, "bound": bound, "work": work, "unit": unit, "ms": ms,
+                "achieved": ach, "peak": peak, "frac": ach / peak if peak else None, "note": note}
+
+    # one RHS: the symmetric form evaluates each pivot pair once; passes of four: every
+    # ordered pair once for the four
+    evals = (st.get("m2l_evals") or st["m2l_pairs"]) if nr == 1 else st["m2l_pairs"]
+    out = [
+        ent("m2l", "k_m2l_sym + k_m2l_cols" if nr == 1 else "k_m2l_group_rhs", "alu", evals, "kernel evaluations",
+            pass_ms[2], MUFU_PER_CLK_SM * sms * clk, "one MUFU rsqrt (or ex2) per kernel evaluation"),
+        ent("l2p_p2p", "k_near_group" if nr == 1 else "k_near_rhs", "alu", st["p2p_pairs"], "point pairs", pass_ms[4],
+            FP32_PER_CLK_SM / NEAR_OPS_PER_PAIR * sms * clk,
+            f"FP32 pipe at {NEAR_OPS_PER_PAIR} lane-ops per pair; includes the FP64 L2P of the same kernel"),
+        ent("p2m_m2m", "k_upward", "hbm", 8 * (op_all + nr * (n + npiv)), "bytes", pass_ms[1], hbm,
+            "FP64 operators of every cell + x in tree order + w; " + hbm_note),
+        ent("l2l", "k_l2l", "hbm", 8 * (op_nonleaf + 2 * nr * npiv), "bytes", pass_ms[3], hbm,
+            "FP64 translations of the non-leaf cells + u read and written; " + hbm_note),
+    ]
+    af = os.path.join(ROOT, "profiles", "aca_invr3d_131k.json")
+    if os.path.exists(af):
+        try:
+            a = json.load(open(af))
+            out.append({"pass": "build_aca", "kernels": "k_aca", "bound": "fp64", "frac": a.get("fp64_pipe_frac"),
+                        "note": a.get("note"), "source": "profiles/aca_invr3d_131k.json"})
+        except Exception:
+            pass
+    return out
 
 
 def run_batch(args):
@@ -473,7 +530,8 @@ def run_batch(args):
         return
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_gpair = MUFU_PER_CLK_SM * SMS * sm_max * 1e6 / 1e9
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak_gpair = MUFU_PER_CLK_SM * sms * sm_max * 1e6 / 1e9
     achieved = m2l_pairs * b.nrhs / (total_ms / args.steps / 1e3) / 1e9
     out = {
         "metric": "batched H2 matvec points/s, 32 uneven problems, FP32 form", "value": value, "unit": "points/s",
