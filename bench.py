@@ -49,6 +49,16 @@ FP32_PER_CLK_SM = 128         # FP32 lanes per SM per clock
 NEAR_OPS_PER_PAIR = 13        # FP32 lane-ops per near-field pair (hi/lo differences, squares, rsqrt scale, fma)
 
 
+# timed arithmetic forms: name -> (nnca precision code, dtype label, description)
+PRECISIONS = {
+    "fp32": (1, "f32", "FP32 kernel evaluations (M2L, P2P), FP64 bases"),
+    "tf32x3": (2, "tf32x3", "tensor-core M2L, 3xTF32 split operands, FP32 accumulation flushed into compensated "
+                            "sums; FP32 P2P; FP64 bases"),
+    "tf32": (3, "tf32", "tensor-core M2L, TF32 operands, FP32 accumulation; FP32 P2P; FP64 bases"),
+    "bf16": (4, "bf16", "tensor-core M2L, BF16 operands, FP32 accumulation; FP32 P2P; FP64 bases"),
+}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -64,6 +74,9 @@ def parse():
                     help="the headline is invr3d_1m; batch32: 32 independent problems in one captured graph; "
                          "fredholm3d: GMRES on the Nystrom system of the second-kind equation")
     ap.add_argument("--no-tune", action="store_true", help="batch32: keep leaf size 64 instead of tuning it")
+    ap.add_argument("--precision", default="fp32", choices=list(PRECISIONS),
+                    help="arithmetic of the timed product: fp32 (SIMT FP32 evaluations), or a tensor-core form "
+                         "for many right-hand sides (tf32x3, tf32, bf16)")
     return ap.parse_args()
 
 
@@ -261,15 +274,16 @@ def run_ours(args):
     x = torch.as_tensor(xh, device="cuda")
     y32 = torch.empty_like(x)
     y64 = torch.empty_like(x)
+    prec, dtype_label, form = PRECISIONS[args.precision]
     h.matvec(x, nnca.PREC_FP64, out=y64)
-    h.matvec(x, nnca.PREC_FP32, out=y32)
+    h.matvec(x, prec, out=y32)
     torch.cuda.synchronize()
     y64h, y32h = y64.cpu().numpy(), y32.cpu().numpy()
     err32 = float(np.linalg.norm(y32h - y64h) / np.linalg.norm(y64h))
 
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")   # 256 MiB > L2
     for _ in range(args.warmup):
-        h.matvec(x, nnca.PREC_FP32, out=y32)
+        h.matvec(x, prec, out=y32)
     torch.cuda.synchronize()
 
     # timed region: K products, CUDA events around each, L2 flushed before each
@@ -285,7 +299,7 @@ def run_ours(args):
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
-        h.matvec(x, nnca.PREC_FP32, out=y32)
+        h.matvec(x, prec, out=y32)
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
@@ -312,11 +326,11 @@ def run_ours(args):
     ypin = torch.empty(N * nrhs, dtype=torch.float64, pin_memory=True)
     xpin.numpy()[:] = np.asarray(xh, dtype=np.float64).ravel()
     e2e_steps = max(3, args.steps // 2)
-    nnca.nnca_matvec_host(h.handle, xpin.numpy(), ypin.numpy(), nrhs, N, nnca.PREC_FP32, stream)
+    nnca.nnca_matvec_host(h.handle, xpin.numpy(), ypin.numpy(), nrhs, N, prec, stream)
     barrier(ws)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        nnca.nnca_matvec_host(h.handle, xpin.numpy(), ypin.numpy(), nrhs, N, nnca.PREC_FP32, stream)
+        nnca.nnca_matvec_host(h.handle, xpin.numpy(), ypin.numpy(), nrhs, N, prec, stream)
     e2e_s = reduce_max(ws, time.perf_counter() - t0)
     e2e_value = ws * N * nrhs * e2e_steps / e2e_s
     yh_e2e = ypin.numpy().copy().reshape((nrhs, N) if nrhs > 1 else (N,))
@@ -346,7 +360,9 @@ def run_ours(args):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     peak_gpair = MUFU_PER_CLK_SM * sms * sm_max * 1e6 / 1e9
-    passes = pass_rooflines(h, st, pass_ms, sms, sm_max, peaks, nrhs if nrhs < 4 else 4)
+    tc = args.precision != "fp32"
+    passes = pass_rooflines(h, st, pass_ms, sms, sm_max, peaks, min(nrhs, 64) if tc else (nrhs if nrhs < 4 else 4),
+                            args.precision)
     # kernel evaluations of the pass: each pivot pair once in the symmetric form
     # (a value serves the row and the column sum), else every ordered pair
     evals = st.get("m2l_evals") or st["m2l_pairs"]
@@ -370,8 +386,8 @@ def run_ours(args):
     out = {
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_desc(w), "form": "FP32 kernel evaluations (M2L, P2P), FP64 bases",
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype_label, "data": "synthetic",
+        "config": {"workload": workload_desc(w), "form": form,
                    "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas x{ws}"},
         "rel_err_fp32_vs_fp64": err32, "rel_err_fp64_vs_dense_256rows": err_dense,
         "rel_err_fp32_vs_dense_256rows": err_dense32,
@@ -393,6 +409,7 @@ def run_ours(args):
                      "traffic_note": ("DRAM bytes read + written by one M2L launch: " + traffic_note) if traffic_note
                      else "no full-size ncu DRAM figure for this kernel and workload"},
         "roofline_passes": passes,
+        "dominant_pass": max((p for p in passes if p.get("ms")), key=lambda p: p["ms"])["pass"],
         "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": N * nrhs * 8,
                 "d2h_bytes_per_step": N * nrhs * 8, "matches_device_result": e2e_ok},
         "gpu_launches": int(st_prof["launches_per_product"]) * args.steps,
@@ -407,7 +424,7 @@ def run_ours(args):
         sys.exit(3)
 
 
-def pass_rooflines(h, st, pass_ms, sms, sm_mhz, peaks, nr):
+def pass_rooflines(h, st, pass_ms, sms, sm_mhz, peaks, nr, precision="fp32"):
     """Achieved fraction of its roofline for every pass of one FP32 product (pass
     times from CUDA events on the launching stream; nr right-hand sides per pass).
 
@@ -438,15 +455,28 @@ def pass_rooflines(h, st, pass_ms, sms, sm_mhz, peaks, nr):
     # one RHS: the symmetric form evaluates each pivot pair once; passes of four: every
     # ordered pair once for the four
     evals = (st.get("m2l_evals") or st["m2l_pairs"]) if nr == 1 else st["m2l_pairs"]
+    if precision != "fp32":
+        # tensor-core M2L: useful flops of the contraction (2 per pivot pair and
+        # right-hand side, times the products per pair), against the tf32 dense
+        # peak = measured bf16 peak x nominal tf32/bf16 ratio (1.1 / 2.25)
+        prods = 3 if precision == "tf32x3" else 1
+        bf16 = float(peaks.get("bf16_tflops", 1900.0)) * 1e12
+        m2l = ent("m2l", "k_m2l_tc (+ pack, unpack)", "tensor", 2.0 * prods * st["m2l_pairs"] * nr, "flops", pass_ms[2],
+                  bf16 * 1.1 / 2.25, f"{prods} tf32 products per pivot pair and right-hand side, {nr} right-hand "
+                  "sides per pass; peak: measured bf16 x 1.1/2.25" + ("" if "bf16_tflops" in peaks else " (fallback)"))
+        m2l["mufu_frac"] = st["m2l_pairs"] / (pass_ms[2] / 1e3) / (MUFU_PER_CLK_SM * sms * clk) if pass_ms[2] else None
+    else:
+        m2l = ent("m2l", "k_m2l_sym + k_m2l_cols" if nr == 1 else "k_m2l_group_rhs", "alu", evals, "kernel evaluations",
+                  pass_ms[2], MUFU_PER_CLK_SM * sms * clk, "one MUFU rsqrt (or ex2) per kernel evaluation")
     out = [
-        ent("m2l", "k_m2l_sym + k_m2l_cols" if nr == 1 else "k_m2l_group_rhs", "alu", evals, "kernel evaluations",
-            pass_ms[2], MUFU_PER_CLK_SM * sms * clk, "one MUFU rsqrt (or ex2) per kernel evaluation"),
-        ent("l2p_p2p", "k_near_group" if nr == 1 else "k_near_rhs", "alu", st["p2p_pairs"], "point pairs", pass_ms[4],
-            FP32_PER_CLK_SM / NEAR_OPS_PER_PAIR * sms * clk,
-            f"FP32 pipe at {NEAR_OPS_PER_PAIR} lane-ops per pair; includes the FP64 L2P of the same kernel"),
-        ent("p2m_m2m", "k_upward", "hbm", 8 * (op_all + nr * (n + npiv)), "bytes", pass_ms[1], hbm,
+        m2l,
+        ent("l2p_p2p", "k_near_group" if nr == 1 else "k_near_rhs", "alu", st["p2p_pairs"] * max(1, nr // 4),
+            "point pairs (evaluations)", pass_ms[4], FP32_PER_CLK_SM / NEAR_OPS_PER_PAIR * sms * clk,
+            f"FP32 pipe at {NEAR_OPS_PER_PAIR} lane-ops per pair, one evaluation per pair and group of up to 4 "
+            "right-hand sides; includes the FP64 L2P of the same kernel"),
+        ent("p2m_m2m", "k_upward", "hbm", 8 * (op_all * max(1, nr // 4) + nr * (n + npiv)), "bytes", pass_ms[1], hbm,
             "FP64 operators of every cell + x in tree order + w; " + hbm_note),
-        ent("l2l", "k_l2l", "hbm", 8 * (op_nonleaf + 2 * nr * npiv), "bytes", pass_ms[3], hbm,
+        ent("l2l", "k_l2l", "hbm", 8 * (op_nonleaf * max(1, nr // 4) + 2 * nr * npiv), "bytes", pass_ms[3], hbm,
             "FP64 translations of the non-leaf cells + u read and written; " + hbm_note),
     ]
     af = os.path.join(ROOT, "profiles", "aca_invr3d_131k.json")

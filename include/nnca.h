@@ -83,8 +83,20 @@ enum { NNCA_F64 = 0, NNCA_F32 = 1 };                 /* element type of x and y 
 /* Arithmetic of the product. FP64: everything in double. FP32: the kernel
  * evaluations of M2L and P2P (nearly all of the work) in float, with
  * coordinates relative to their cell centre and compensated accumulation
- * across source cells; bases, translations and coefficient vectors in double. */
-enum { NNCA_PREC_FP64 = 0, NNCA_PREC_FP32 = 1 };
+ * across source cells; bases, translations and coefficient vectors in double.
+ * Tensor-core forms (for many right-hand sides; radial kernels, d <= 3): the
+ * FP32 form with the M2L of up to 64 right-hand sides at once as dense
+ * contractions on the tensor cores (tcgen05.mma), the kernel values K
+ * evaluated on the fly in float and multiplied with the multipole
+ * coefficients of all right-hand sides, accumulated in FP32 in tensor memory:
+ *   NNCA_PREC_TF32X3  both operands split into tf32 hi + lo parts, three
+ *                     products per pair (hi hi + hi lo + lo hi; about 22 bits);
+ *   NNCA_PREC_TF32    one tf32 product per pair (11-bit operands);
+ *   NNCA_PREC_BF16    both operands rounded to bfloat16, one product per pair
+ *                     (8-bit operands, FP32 accumulation).
+ * The other passes run as in the FP32 form. nnca_matvec_noalloc takes FP64 and
+ * FP32 only. */
+enum { NNCA_PREC_FP64 = 0, NNCA_PREC_FP32 = 1, NNCA_PREC_TF32X3 = 2, NNCA_PREC_TF32 = 3, NNCA_PREC_BF16 = 4 };
 /* nnca_config.m2l_form */
 enum { NNCA_M2L_AUTO = 0, NNCA_M2L_FULL = 1 };
 
@@ -155,9 +167,10 @@ nnca_status nnca_build(const nnca_config *cfg, const double *P, int64_t nP, cons
 
 /* y = A~ x for nrhs right-hand sides. x, y: device pointers, element type
  * dtype (NNCA_F64 or NNCA_F32), column r at [r*ld .. r*ld + n). y is
- * overwritten. precision: NNCA_PREC_FP64 (all arithmetic in FP64) or
+ * overwritten. precision: NNCA_PREC_FP64 (all arithmetic in FP64),
  * NNCA_PREC_FP32 (kernel evaluations and contractions in FP32 with
- * cell-relative coordinates and compensated accumulation across cells).
+ * cell-relative coordinates and compensated accumulation across cells), or a
+ * tensor-core form (NNCA_PREC_TF32X3, NNCA_PREC_TF32, NNCA_PREC_BF16).
  * Asynchronous on `stream`. The first call with a larger nrhs than before
  * allocates the handle's workspace (so make that call before capturing a
  * stream into a graph). */

@@ -1378,6 +1378,33 @@ void build_finish(Handle *h) {
             NNCA_CUDA(cudaMemcpy(h->m2l_item_part, full.part.data(), full.part.size() * sizeof(int),
                                  cudaMemcpyHostToDevice));
         }
+        // tensor-core M2L items: at most 64 targets of one parent's children, each
+        // over the parent's whole full-form plan, heaviest first
+        if (np > 0 && !h->m2l_fp32_unsupported) {
+            std::vector<std::pair<int64_t, int4>> tci;
+            for (int64_t i = 0; i < np; ++i) {
+                const int P = parents[i];
+                const int64_t T = hpo[hche[P]] - hpo[hchb[P]];
+                const int64_t k0 = roff[i], nk = roff[i + 1] - roff[i];
+                if (nk == 0 || T == 0) continue;
+                int64_t src = 0;
+                for (int64_t k = k0; k < k0 + nk; ++k) src += 2 * ((hplan[k].z >> 11) & 0x7ff);
+                for (int64_t t0 = 0; t0 < T; t0 += 64) {
+                    const int nt = (int)std::min<int64_t>(64, T - t0);
+                    tci.push_back({(int64_t)nt * src, make_int4(P, (int)t0 | (nt << 16), (int)k0, (int)nk)});
+                }
+            }
+            std::stable_sort(tci.begin(), tci.end(),
+                             [](const std::pair<int64_t, int4> &a, const std::pair<int64_t, int4> &b) {
+                                 return a.first > b.first;
+                             });
+            std::vector<int4> tcv(tci.size());
+            for (size_t i = 0; i < tci.size(); ++i) tcv[i] = tci[i].second;
+            h->n_tc_items = (int)tcv.size();
+            h->tc_items = dalloc<int4>(h, tcv.size());
+            if (!tcv.empty())
+                NNCA_CUDA(cudaMemcpy(h->tc_items, tcv.data(), tcv.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        }
         h->n_m2l_split = (int)full.splits.size();
         h->m2l_split = dalloc<int4>(h, full.splits.size());
         h->m2l_parts = dalloc<double>(h, (size_t)std::max(full.nparts, 1) * M2L_GROUP_TARGETS * M2L_RHS);

@@ -239,7 +239,7 @@ nnca_status nnca_matvec(nnca_handle h, const void *x, void *y, int64_t nrhs, int
     if (nrhs < 1) return fail(h, NNCA_ERR_INVALID_ARG, "nnca_matvec: nrhs must be >= 1");
     if (ld < h->n) return fail(h, NNCA_ERR_INVALID_ARG, "nnca_matvec: ld must be >= n");
     if (dtype != NNCA_F64 && dtype != NNCA_F32) return fail(h, NNCA_ERR_INVALID_ARG, "nnca_matvec: unknown dtype");
-    if (precision != NNCA_PREC_FP64 && precision != NNCA_PREC_FP32)
+    if (precision < NNCA_PREC_FP64 || precision > NNCA_PREC_BF16)
         return fail(h, NNCA_ERR_INVALID_ARG, "nnca_matvec: unknown precision");
     if (!is_device_ptr(x) || !is_device_ptr(y))
         return fail(h, NNCA_ERR_INVALID_ARG, "nnca_matvec: x and y must be device memory");
@@ -292,7 +292,7 @@ nnca_status nnca_matvec_batch(const nnca_handle *hs, int count, const void *cons
     if (count < 1 || count > 4096) return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_matvec_batch: count must be 1..4096");
     if (nrhs < 1) return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_matvec_batch: nrhs must be >= 1");
     if (dtype != NNCA_F64 && dtype != NNCA_F32) return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_matvec_batch: unknown dtype");
-    if (precision != NNCA_PREC_FP64 && precision != NNCA_PREC_FP32)
+    if (precision < NNCA_PREC_FP64 || precision > NNCA_PREC_BF16)
         return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_matvec_batch: unknown precision");
     std::set<const void *> seen;
     for (int k = 0; k < count; ++k) {
@@ -364,6 +364,7 @@ nnca_status nnca_matvec_host(nnca_handle h, const void *x_host, void *y_host, in
 nnca_status nnca_set_wait_test(int64_t wait_limit_clocks, unsigned extra_tx_bytes) {
     try {
         set_wait_test(wait_limit_clocks, extra_tx_bytes);
+        set_wait_test_tc(wait_limit_clocks, extra_tx_bytes);
     } catch (const Error &e) {
         return fail(nullptr, e.status, e.what());
     }

@@ -31,83 +31,7 @@ namespace nnca {
 
 namespace {
 
-// Single-instruction MUFU forms (flush-to-zero approximations).
-__device__ __forceinline__ float mufu_rsqrt(float x) {
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float mufu_ex2(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float mufu_lg2(float x) {
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// f(r^2) with K = s f(r); FP32 and FP64 forms, one instantiation per kernel.
-// f32_far: r^2 > 0 guaranteed (distinct cells); f32: any r^2 >= 0.
-template <int KIND> struct KF;
-template <> struct KF<NNCA_K_INV_R> {
-    static __device__ __forceinline__ float f32(const KParams &, float r2) { return r2 > 0.f ? mufu_rsqrt(r2) : 0.f; }
-    static __device__ __forceinline__ float f32_far(const KParams &, float r2) { return mufu_rsqrt(r2); }
-    static __device__ __forceinline__ double f64(const KParams &, double r2) { return r2 > 0.0 ? rsqrt(r2) : 0.0; }
-};
-template <> struct KF<NNCA_K_LOG> {
-    // 0.5 ln(r^2) = (0.5 ln 2) log2(r^2)
-    static __device__ __forceinline__ float f32(const KParams &, float r2) {
-        return r2 > 0.f ? 0.34657359f * mufu_lg2(r2) : 0.f;
-    }
-    static __device__ __forceinline__ float f32_far(const KParams &, float r2) { return 0.34657359f * mufu_lg2(r2); }
-    static __device__ __forceinline__ double f64(const KParams &, double r2) { return r2 > 0.0 ? 0.5 * log(r2) : 0.0; }
-};
-template <> struct KF<NNCA_K_GAUSS> {
-    // exp(-r^2 / (2 h^2)) = 2^(r^2 * c), c = -log2(e) / (2 h^2) precomputed in kp.hf
-    static __device__ __forceinline__ float f32(const KParams &kp, float r2) { return mufu_ex2(r2 * kp.hf); }
-    static __device__ __forceinline__ float f32_far(const KParams &kp, float r2) { return mufu_ex2(r2 * kp.hf); }
-    static __device__ __forceinline__ double f64(const KParams &kp, double r2) { return exp(-r2 / (2.0 * kp.h * kp.h)); }
-};
-template <> struct KF<NNCA_K_MATERN> {
-    static __device__ __forceinline__ float f32(const KParams &kp, float r2) { return __expf(-sqrtf(r2) / (float)kp.h); }
-    static __device__ __forceinline__ float f32_far(const KParams &kp, float r2) { return f32(kp, r2); }
-    static __device__ __forceinline__ double f64(const KParams &kp, double r2) { return exp(-sqrt(r2) / kp.h); }
-};
-template <> struct KF<NNCA_K_PAPER_I> {
-    static __device__ __forceinline__ float f32(const KParams &kp, float r2) {
-        if (!(r2 > 0.f)) return 0.f;
-        const float a = (float)kp.h, r = sqrtf(r2);
-        return r < a ? (r * (logf(r) - 1.f)) / (a * (logf(a) - 1.f)) : logf(r) / logf(a);
-    }
-    static __device__ __forceinline__ float f32_far(const KParams &kp, float r2) { return f32(kp, r2); }
-    static __device__ __forceinline__ double f64(const KParams &kp, double r2) {
-        if (!(r2 > 0.0)) return 0.0;
-        const double a = kp.h, r = sqrt(r2);
-        return r < a ? (r * (log(r) - 1.0)) / (a * (log(a) - 1.0)) : log(r) / log(a);
-    }
-};
-template <> struct KF<NNCA_K_PAPER_II> {
-    static __device__ __forceinline__ float f32(const KParams &kp, float r2) {
-        const float a = (float)kp.h, r = sqrtf(r2);
-        return r < a ? r / a : a / r;
-    }
-    static __device__ __forceinline__ float f32_far(const KParams &kp, float r2) { return f32(kp, r2); }
-    static __device__ __forceinline__ double f64(const KParams &kp, double r2) {
-        const double a = kp.h, r = sqrt(r2);
-        return r < a ? r / a : a / r;
-    }
-};
-
-// compensated accumulation: (s, c) += v
-__device__ __forceinline__ void two_sum_add(float &s, float &c, float v) {
-    const float t = s + v;
-    const float bp = t - s;
-    const float err = (s - (t - bp)) + (v - bp);
-    s = t;
-    c += err;
-}
+#include "dev_common.cuh"
 
 unsigned grid_for(int64_t n, int threads, int64_t cap = 152 * 64) {
     int64_t g = (n + threads - 1) / threads;
@@ -371,84 +295,6 @@ __global__ void __launch_bounds__(32 * MV_WARPS) k_m2l_f64(KParams kp, int d, co
     }
 }
 
-// ---- packed FP32 arithmetic (two lanes of float in one 64-bit register) ------
-typedef unsigned long long f2;
-__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ float2 f2_unpack(f2 a) {
-    float2 r;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a));
-    return r;
-}
-__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
-    f2 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
-    f2 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
-    f2 r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
-    f2 r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-
-// f(r^2) on a packed pair; SAFE maps r^2 = 0 to f(0) of the singular kernels (0).
-#ifndef NNCA_RSQRT_NEWTON
-#define NNCA_RSQRT_NEWTON 0
-#endif
-template <int KIND, bool SAFE> struct KF2 {
-    static __device__ __forceinline__ f2 eval(const KParams &kp, f2 r2) {
-        const float2 v = f2_unpack(r2);
-        return f2_pack(SAFE ? KF<KIND>::f32(kp, v.x) : KF<KIND>::f32_far(kp, v.x),
-                       SAFE ? KF<KIND>::f32(kp, v.y) : KF<KIND>::f32_far(kp, v.y));
-    }
-};
-// rsqrt of both halves of a packed pair, unpacked and repacked inside one PTX
-// block so that the halves can stay in their register pair
-__device__ __forceinline__ f2 f2_rsqrt(f2 a) {
-    f2 r;
-    asm("{\n\t.reg .f32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\trsqrt.approx.ftz.f32 lo, lo;\n\t"
-        "rsqrt.approx.ftz.f32 hi, hi;\n\tmov.b64 %0, {lo, hi};\n\t}"
-        : "=l"(r)
-        : "l"(a));
-    return r;
-}
-
-template <bool SAFE> struct KF2<NNCA_K_INV_R, SAFE> {
-    // 1/r: one MUFU rsqrt (relative error ~1e-7). An optional Newton step
-    // f <- f - (f/2)(r^2 f^2 - 1) takes it to float rounding, at 4 more packed
-    // operations per pair; measured, it changes the product's error by ~3%.
-    static __device__ __forceinline__ f2 eval(const KParams &, f2 r2) {
-        f2 f = f2_rsqrt(r2);
-#if NNCA_RSQRT_NEWTON
-        const f2 h = f2_mul(r2, f);
-        const f2 e = f2_fma(h, f, f2_pack(-1.f, -1.f));
-        const f2 hf = f2_mul(f, f2_pack(-0.5f, -0.5f));
-        f = f2_fma(hf, e, f);
-#endif
-        if (SAFE) {
-            const float2 v = f2_unpack(r2);
-            float2 g = f2_unpack(f);
-            g.x = v.x > 0.f ? g.x : 0.f;
-            g.y = v.y > 0.f ? g.y : 0.f;
-            f = f2_pack(g.x, g.y);
-        }
-        return f;
-    }
-};
-
 // ---- FP32 source streaming -----------------------------------------------------
 // A warp streams the sources of its source cells through a 64-entry ring in
 // shared memory and evaluates them in full chunks of 32. Sources are stored in
@@ -624,52 +470,6 @@ __device__ __forceinline__ void stage_note(M2lSymSmem &S, int b, unsigned bytes)
         S.rsrc[b] = n;
         S.scol += n;
     }
-}
-
-__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(void *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(void *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_tx(void *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-// The bounded waits' clock budget and the bytes added to every staging round's
-// expected transaction count, in device memory so that a test can change them
-// (nnca_set_wait_test): 2^31 clocks and 0 in normal use. With extra bytes the
-// rounds' phases never complete although every copy lands, so every wait on
-// them runs out.
-__device__ long long g_wait_limit = 1ll << 31;
-__device__ unsigned g_stage_extra_tx = 0u;
-
-// wait until the phase of the given parity has completed; false after g_wait_limit clocks
-__device__ __forceinline__ bool mbar_wait(void *bar, unsigned parity) {
-    const unsigned a = smem_addr(bar);
-    const long long lim = g_wait_limit;
-    const long long t0 = clock64();
-    for (;;) {
-        unsigned ok;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(ok)
-                     : "r"(a), "r"(parity)
-                     : "memory");
-        if (ok) return true;
-        if (clock64() - t0 > lim) return false;
-    }
-}
-// the same wait taken by a whole warp: it succeeds only if it succeeds for every lane
-__device__ __forceinline__ bool mbar_wait_warp(void *bar, unsigned parity) {
-    return __all_sync(0xffffffffu, mbar_wait(bar, parity));
-}
-// bulk copy global -> shared (16-byte aligned, size a multiple of 16), completing on bar
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, void *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
 }
 
 // The staging warp's copy of the plan records of the next round: lane i holds
@@ -2358,82 +2158,64 @@ void ensure_workspace(Handle *h, int64_t nrhs) {
     h->ws_nrhs = nrhs;
 }
 
-// One group of NR right-hand sides. FP32 == true selects FP32 kernel evaluations.
-template <bool FP32, int NR, int KIND, class TO>
-void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
-    cudaStream_t s = h->stream;
-    const int64_t N = h->n, npiv = h->npiv;
-    double *xt = (double *)h->ws;
-    double *w = xt + NR * N;
-    double *u = w + NR * npiv;
-    float *xt32 = FP32 ? (float *)(u + NR * npiv) : nullptr;
-    // FP32: the weights go straight into the packed M2L sources (one right-hand
-    // side) or into the packed weights of an M2L_RHS pass
-    const bool f32 = FP32 && kernel_is_radial(h->kp.kind);
-    float *spk_w = f32 && NR == 1 ? reinterpret_cast<float *>(h->spk) : nullptr;
-    float *spw = f32 && NR == M2L_RHS ? reinterpret_cast<float *>(h->spw) : nullptr;
-    const TO *xin = (const TO *)x + r0 * ld;
-    TO *yout = (TO *)y + r0 * ld;
-    prof_mark(h, 0);
-    float *ppk_w = f32 && NR == 1 && h->near_packed ? reinterpret_cast<float *>(h->ppk) : nullptr;
+// The passes of one group of NR right-hand sides (vectors right-hand-side major,
+// NR rows of N or npiv).
+
+// a14: x (caller order) into tree order (FP64 and, for the FP32 form, FP32);
+// near_w: the float weights of the packed near-field pairs too (one right-hand side)
+template <int NR, class TO>
+void pass_perm(Handle *h, const TO *xin, int64_t ld, double *xt, float *xt32, bool near_w) {
+    float *ppk_w = near_w ? reinterpret_cast<float *>(h->ppk) : nullptr;
     float *ppl_w = ppk_w ? reinterpret_cast<float *>(h->ppl) : nullptr;
-    k_perm_in<TO><<<grid_for(N * NR, 256), 256, 0, s>>>(xin, ld, N, NR, h->perm, xt, xt32, ppk_w, ppl_w, h->leaf_of,
-                                                        h->cbeg, h->ppk_off);
+    k_perm_in<TO><<<grid_for(h->n * NR, 256), 256, 0, h->stream>>>(xin, ld, h->n, NR, h->perm, xt, xt32, ppk_w, ppl_w,
+                                                                 h->leaf_of, h->cbeg, h->ppk_off);
     NNCA_LAUNCH_CHECK();
     ++h->launches;
-    prof_mark(h, 1);
+}
+
+// a8, a9: P2M on the leaves, then M2M level by level (FP64 operators); spk_w,
+// spw: the float weights of the FP32 M2L's packed sources (one or M2L_RHS
+// right-hand sides), or null
+template <int NR>
+void pass_up(Handle *h, const double *xt, double *w, float *spk_w, float *spw) {
+    cudaStream_t s = h->stream;
+    const int64_t N = h->n, npiv = h->npiv;
     const double *op = h->op;
-    if (npiv > 0) NNCA_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * NR * npiv, s));
-    if (h->lmin <= h->kappa && npiv > 0) {
-        const int64_t lb = h->level_base[h->kappa], le = h->level_base[h->kappa + 1];
-        k_upward<double, NR, 1><<<grid_for(le - lb, UP_THREADS / 32), UP_THREADS, 0, s>>>(lb, le, 1, h->cbeg, h->cend, h->cch_beg,
-                                                                           h->cch_end, h->piv_off, h->op_off, op, xt,
-                                                                           N, w, npiv, spk_w, h->spk_off, spw);
-        NNCA_LAUNCH_CHECK();
+    const int64_t lb = h->level_base[h->kappa], le = h->level_base[h->kappa + 1];
+    k_upward<double, NR, 1><<<grid_for(le - lb, UP_THREADS / 32), UP_THREADS, 0, s>>>(
+        lb, le, 1, h->cbeg, h->cend, h->cch_beg, h->cch_end, h->piv_off, h->op_off, op, xt, N, w, npiv, spk_w,
+        h->spk_off, spw);
+    NNCA_LAUNCH_CHECK();
+    ++h->launches;
+    for (int l = h->kappa - 1; l >= h->lmin; --l) {
+        const int64_t b0 = h->level_base[l], b1 = h->level_base[l + 1];
         ++h->launches;
-        for (int l = h->kappa - 1; l >= h->lmin; --l) {
-            const int64_t b0 = h->level_base[l], b1 = h->level_base[l + 1];
-            ++h->launches;
-            k_upward<double, NR, UP_THREADS / 32><<<grid_for(b1 - b0, 1), UP_THREADS, 0, s>>>(b0, b1, 0, h->cbeg, h->cend,
-                                                                               h->cch_beg, h->cch_end, h->piv_off,
-                                                                               h->op_off, op, xt, N, w, npiv, spk_w,
-                                                                               h->spk_off, spw);
-            NNCA_LAUNCH_CHECK();
-        }
-        prof_mark(h, 2);
-        if (h->n_m2l_tgt > 0) {
-            const unsigned g = grid_for(h->n_m2l_tgt, MV_WARPS, 152 * 16);
-            if (!(FP32 && kernel_is_radial(h->kp.kind))) ++h->launches;
-            if (!kernel_is_radial(h->kp.kind)) {
-                k_m2l_generic<NR><<<grid_for(h->n_m2l_tgt * 32, 128), 128, 0, s>>>(
-                    h->kp, h->d, h->m2l_tgt, h->n_m2l_tgt, h->il_off, h->il_idx, h->piv_off, h->pv64, npiv, w, u);
-            } else if (FP32 && NR == 1 && h->sym_items) {
-                launch_m2l_sym<KIND>(h, w, u);
-            } else if (FP32 && NR == 1) {
-                launch_m2l_f32<KIND>(h, u);
-            } else if (FP32 && NR == M2L_RHS) {
-                launch_m2l_f32_rhs<KIND>(h, u);
-            } else {
-                k_m2l_f64<KIND, NR><<<g, 32 * MV_WARPS, 0, s>>>(h->kp, h->d, h->m2l_tgt, h->n_m2l_tgt, h->il_off,
-                                                                h->il_idx, h->piv_off, h->pv64, npiv, w, u);
-            }
-            NNCA_LAUNCH_CHECK();
-        }
-        prof_mark(h, 3);
-        for (int l = h->lmin + 1; l <= h->kappa; ++l) {
-            // parents at level l - 1 push down to their children at level l
-            const int64_t p0 = h->level_base[l - 1], p1 = h->level_base[l];
-            ++h->launches;
-            k_l2l<double, NR><<<grid_for(p1 - p0, 1), UP_THREADS, 0, s>>>(p0, p1, h->cch_beg, h->cch_end, h->piv_off,
-                                                                             h->op_off, op, u, npiv);
-            NNCA_LAUNCH_CHECK();
-        }
+        k_upward<double, NR, UP_THREADS / 32><<<grid_for(b1 - b0, 1), UP_THREADS, 0, s>>>(
+            b0, b1, 0, h->cbeg, h->cend, h->cch_beg, h->cch_end, h->piv_off, h->op_off, op, xt, N, w, npiv, spk_w,
+            h->spk_off, spw);
+        NNCA_LAUNCH_CHECK();
     }
-    else {
-        prof_mark(h, 2);
-        prof_mark(h, 3);
+}
+
+// a11: L2L, parents at level l - 1 push down to their children at level l
+template <int NR>
+void pass_l2l(Handle *h, double *u) {
+    for (int l = h->lmin + 1; l <= h->kappa; ++l) {
+        const int64_t p0 = h->level_base[l - 1], p1 = h->level_base[l];
+        ++h->launches;
+        k_l2l<double, NR><<<grid_for(p1 - p0, 1), UP_THREADS, 0, h->stream>>>(p0, p1, h->cch_beg, h->cch_end,
+                                                                              h->piv_off, h->op_off, h->op, u,
+                                                                              h->npiv);
+        NNCA_LAUNCH_CHECK();
     }
-    prof_mark(h, 4);
+}
+
+// a12, a13: L2P fused with P2P, output in caller order
+template <bool FP32, int NR, int KIND, class TO>
+void pass_near(Handle *h, const double *u, const double *xt, const float *xt32, TO *yout, int64_t ld) {
+    cudaStream_t s = h->stream;
+    const int64_t N = h->n, npiv = h->npiv;
+    const double *op = h->op;
     if (!(FP32 && kernel_is_radial(h->kp.kind))) ++h->launches;
     const unsigned gl = grid_for(h->nleaf, MV_WARPS, 152 * 16);
     if (!kernel_is_radial(h->kp.kind)) {
@@ -2467,7 +2249,148 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
                                                               h->xs, N, xt, h->perm, yout, ld);
     }
     NNCA_LAUNCH_CHECK();
+}
+
+// One group of NR right-hand sides. FP32 == true selects FP32 kernel evaluations.
+template <bool FP32, int NR, int KIND, class TO>
+void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
+    cudaStream_t s = h->stream;
+    const int64_t N = h->n, npiv = h->npiv;
+    double *xt = (double *)h->ws;
+    double *w = xt + NR * N;
+    double *u = w + NR * npiv;
+    float *xt32 = FP32 ? (float *)(u + NR * npiv) : nullptr;
+    // FP32: the weights go straight into the packed M2L sources (one right-hand
+    // side) or into the packed weights of an M2L_RHS pass
+    const bool f32 = FP32 && kernel_is_radial(h->kp.kind);
+    float *spk_w = f32 && NR == 1 ? reinterpret_cast<float *>(h->spk) : nullptr;
+    float *spw = f32 && NR == M2L_RHS ? reinterpret_cast<float *>(h->spw) : nullptr;
+    const TO *xin = (const TO *)x + r0 * ld;
+    TO *yout = (TO *)y + r0 * ld;
+    prof_mark(h, 0);
+    pass_perm<NR, TO>(h, xin, ld, xt, xt32, f32 && NR == 1 && h->near_packed);
+    prof_mark(h, 1);
+    if (npiv > 0) NNCA_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * NR * npiv, s));
+    if (h->lmin <= h->kappa && npiv > 0) {
+        pass_up<NR>(h, xt, w, spk_w, spw);
+        prof_mark(h, 2);
+        if (h->n_m2l_tgt > 0) {
+            const unsigned g = grid_for(h->n_m2l_tgt, MV_WARPS, 152 * 16);
+            if (!(FP32 && kernel_is_radial(h->kp.kind))) ++h->launches;
+            if (!kernel_is_radial(h->kp.kind)) {
+                k_m2l_generic<NR><<<grid_for(h->n_m2l_tgt * 32, 128), 128, 0, s>>>(
+                    h->kp, h->d, h->m2l_tgt, h->n_m2l_tgt, h->il_off, h->il_idx, h->piv_off, h->pv64, npiv, w, u);
+            } else if (FP32 && NR == 1 && h->sym_items) {
+                launch_m2l_sym<KIND>(h, w, u);
+            } else if (FP32 && NR == 1) {
+                launch_m2l_f32<KIND>(h, u);
+            } else if (FP32 && NR == M2L_RHS) {
+                launch_m2l_f32_rhs<KIND>(h, u);
+            } else {
+                k_m2l_f64<KIND, NR><<<g, 32 * MV_WARPS, 0, s>>>(h->kp, h->d, h->m2l_tgt, h->n_m2l_tgt, h->il_off,
+                                                                h->il_idx, h->piv_off, h->pv64, npiv, w, u);
+            }
+            NNCA_LAUNCH_CHECK();
+        }
+        prof_mark(h, 3);
+        pass_l2l<NR>(h, u);
+    } else {
+        prof_mark(h, 2);
+        prof_mark(h, 3);
+    }
+    prof_mark(h, 4);
+    pass_near<FP32, NR, KIND, TO>(h, u, xt, xt32, yout, ld);
     prof_mark(h, 5);
+}
+
+// The tensor-core forms: passes of up to tc_rhs_per_pass() right-hand sides.
+// Per pass: the permutation and the upward pass for all of its right-hand
+// sides (groups of M2L_RHS, FP64 operators), one tensor-core M2L for all of
+// them, then L2L and the near field (the FP32 kernels) group by group.
+template <int KIND, class TO>
+void run_tc(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int mode) {
+    cudaStream_t s = h->stream;
+    const int64_t N = h->n, npiv = h->npiv;
+    const int RW = tc_rhs_per_pass();
+    double *xt = (double *)h->tc_ws;
+    double *w = xt + (size_t)RW * N;
+    double *u = w + (size_t)RW * npiv;
+    float *xt32 = (float *)(u + (size_t)RW * npiv);
+    float *tcws = xt32 + (size_t)RW * N;
+    for (int64_t p0 = 0; p0 < nrhs; p0 += RW) {
+        const int nr = (int)std::min<int64_t>(RW, nrhs - p0);
+        const TO *xin = (const TO *)x + p0 * ld;
+        TO *yout = (TO *)y + p0 * ld;
+        prof_mark(h, 0);
+        for (int r = 0; r < nr;) {
+            if (nr - r >= M2L_RHS) {
+                pass_perm<M2L_RHS, TO>(h, xin + r * ld, ld, xt + r * N, xt32 + r * N, false);
+                r += M2L_RHS;
+            } else {
+                pass_perm<1, TO>(h, xin + r * ld, ld, xt + r * N, xt32 + r * N, false);
+                r += 1;
+            }
+        }
+        prof_mark(h, 1);
+        const bool far = h->lmin <= h->kappa && npiv > 0;
+        if (far) {
+            for (int r = 0; r < nr;) {
+                if (nr - r >= M2L_RHS) {
+                    pass_up<M2L_RHS>(h, xt + r * N, w + r * npiv, nullptr, nullptr);
+                    r += M2L_RHS;
+                } else {
+                    pass_up<1>(h, xt + r * N, w + r * npiv, nullptr, nullptr);
+                    r += 1;
+                }
+            }
+        }
+        prof_mark(h, 2);
+        if (far) m2l_tensor(h, mode, nr, w, u, tcws);
+        else if (npiv > 0) NNCA_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * nr * npiv, s));
+        prof_mark(h, 3);
+        if (far)
+            for (int r = 0; r < nr;) {
+                if (nr - r >= M2L_RHS) {
+                    pass_l2l<M2L_RHS>(h, u + r * npiv);
+                    r += M2L_RHS;
+                } else {
+                    pass_l2l<1>(h, u + r * npiv);
+                    r += 1;
+                }
+            }
+        prof_mark(h, 4);
+        for (int r = 0; r < nr;) {
+            if (nr - r >= M2L_RHS) {
+                pass_near<true, M2L_RHS, KIND, TO>(h, u + r * npiv, xt + r * N, xt32 + r * N, yout + r * ld, ld);
+                r += M2L_RHS;
+            } else {
+                // one right-hand side: the near-field weights from its tree-order copy
+                if (h->near_packed) {
+                    k_near_weights<<<grid_for(N, 256), 256, 0, s>>>(N, xt + r * N, reinterpret_cast<float *>(h->ppk),
+                                                                    reinterpret_cast<float *>(h->ppl), h->leaf_of,
+                                                                    h->cbeg, h->ppk_off);
+                    NNCA_LAUNCH_CHECK();
+                    ++h->launches;
+                }
+                pass_near<true, 1, KIND, TO>(h, u + r * npiv, xt + r * N, xt32 + r * N, yout + r * ld, ld);
+                r += 1;
+            }
+        }
+        prof_mark(h, 5);
+    }
+}
+
+void ensure_tc_workspace(Handle *h) {
+    const size_t RW = (size_t)tc_rhs_per_pass();
+    const size_t bytes = RW * ((size_t)h->n + 2 * (size_t)h->npiv) * sizeof(double) + RW * (size_t)h->n * sizeof(float) +
+                         tc_workspace_floats(h) * sizeof(float) + 256;
+    if (h->tc_ws && h->tc_ws_bytes >= bytes) return;
+    if (h->tc_ws) dev_free(h, h->tc_ws);
+    h->tc_ws = nullptr;
+    h->tc_ws = dev_alloc(h, bytes);
+    h->tc_ws_bytes = bytes;
+    // the packed weights' padding must read as zero: clear once
+    NNCA_CUDA(cudaMemsetAsync(h->tc_ws, 0, bytes, h->stream));
 }
 
 template <bool FP32, int KIND, class TO>
@@ -2506,6 +2429,19 @@ void set_wait_test(int64_t wait_limit_clocks, unsigned extra_tx_bytes) {
     NNCA_CUDA(cudaDeviceSynchronize());
 }
 
+template <class TO>
+void dispatch_tc(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int mode) {
+    switch (h->kp.kind) {
+    case NNCA_K_INV_R: run_tc<NNCA_K_INV_R, TO>(h, x, y, nrhs, ld, mode); break;
+    case NNCA_K_LOG: run_tc<NNCA_K_LOG, TO>(h, x, y, nrhs, ld, mode); break;
+    case NNCA_K_GAUSS: run_tc<NNCA_K_GAUSS, TO>(h, x, y, nrhs, ld, mode); break;
+    case NNCA_K_MATERN: run_tc<NNCA_K_MATERN, TO>(h, x, y, nrhs, ld, mode); break;
+    case NNCA_K_PAPER_I: run_tc<NNCA_K_PAPER_I, TO>(h, x, y, nrhs, ld, mode); break;
+    case NNCA_K_PAPER_II: run_tc<NNCA_K_PAPER_II, TO>(h, x, y, nrhs, ld, mode); break;
+    default: NNCA_REQUIRE(false, NNCA_ERR_UNSUPPORTED, "the tensor-core forms need a radial kernel");
+    }
+}
+
 void matvec(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int dtype, int precision) {
     const bool radial = kernel_is_radial(h->kp.kind);
     NNCA_REQUIRE(radial || precision == NNCA_PREC_FP64, NNCA_ERR_UNSUPPORTED,
@@ -2514,6 +2450,14 @@ void matvec(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int dty
                  "the FP32 product supports d <= 3");
     NNCA_REQUIRE(!h->m2l_fp32_unsupported || precision == NNCA_PREC_FP64, NNCA_ERR_UNSUPPORTED,
                  h->m2l_fp32_unsupported ? h->m2l_fp32_unsupported : "");
+    const bool tc = precision == NNCA_PREC_TF32X3 || precision == NNCA_PREC_TF32 || precision == NNCA_PREC_BF16;
+    if (tc) {
+        ensure_tc_workspace(h);
+        h->launches = 0;
+        if (dtype == NNCA_F64) dispatch_tc<double>(h, x, y, nrhs, ld, precision);
+        else dispatch_tc<float>(h, x, y, nrhs, ld, precision);
+        return;
+    }
     ensure_workspace(h, std::min<int64_t>(nrhs, 4));
     h->launches = 0;
     if (precision == NNCA_PREC_FP32) {

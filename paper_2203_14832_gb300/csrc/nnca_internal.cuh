@@ -350,6 +350,11 @@ struct Handle {
     int32_t *sym_ent = nullptr;
     int2 *sym_tasks = nullptr;        // (cell with slots, first of 32 pivots) per warp of the column pass
     int n_sym_tasks = 0;
+    // tensor-core M2L of many right-hand sides: items (parent, first target |
+    // targets << 16, first record, records) of at most 64 targets over the full
+    // plan (m2l_plan), heaviest first
+    int4 *tc_items = nullptr;
+    int n_tc_items = 0;
     int2 *leaf_items[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     int n_leaf_items[5] = {0, 0, 0, 0, 0};
 
@@ -357,6 +362,8 @@ struct Handle {
     void *ws = nullptr;
     size_t ws_bytes = 0;
     int64_t ws_nrhs = 0;
+    void *tc_ws = nullptr;        // workspace of the tensor-core forms (passes of 64 right-hand sides)
+    size_t tc_ws_bytes = 0;
     void *host_stage = nullptr;   // device buffers for nnca_matvec_host
     size_t host_stage_bytes = 0;
 
@@ -380,6 +387,13 @@ void build_finish(Handle *h);   // data of the product: centres, FP32 coordinate
 void matvec(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int dtype, int precision);
 // wait budget and extra expected bytes of the FP32 kernels' staging (nnca_set_wait_test)
 void set_wait_test(int64_t wait_limit_clocks, unsigned extra_tx_bytes);
+void set_wait_test_tc(int64_t wait_limit_clocks, unsigned extra_tx_bytes);
+// Tensor-core M2L (m2l_tc.cu) of one pass of nr <= tc_rhs_per_pass() right-hand
+// sides: w and u right-hand-side major FP64 (nr rows of npiv); tcws holds
+// tc_workspace_floats(h) floats. mode: NNCA_PREC_TF32X3, NNCA_PREC_TF32 or NNCA_PREC_BF16.
+int tc_rhs_per_pass();
+size_t tc_workspace_floats(const Handle *h);
+void m2l_tensor(Handle *h, int mode, int nr, const double *w, double *u, float *tcws);
 
 // Exclusive scan of n uint32/int64 values (scan.cu). out may alias in.
 void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s, Scratch &scr);

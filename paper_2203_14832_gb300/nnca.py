@@ -26,7 +26,7 @@ K_LOG, K_INV_R, K_GAUSS, K_MATERN, K_PAPER_I, K_PAPER_II, K_SEPARABLE, K_POLY2 =
 LAYOUT_AOS, LAYOUT_SOA = 0, 1
 M2L_AUTO, M2L_FULL = 0, 1
 F64, F32 = 0, 1
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_TF32X3, PREC_TF32, PREC_BF16 = 0, 1, 2, 3, 4
 EXPORTS = ["PERM", "KEYS", "LEVEL_BASE", "CKEY", "CBEG", "CEND", "CPAR", "CCH_BEG", "CCH_END", "NB_OFF", "NB_IDX",
            "IL_OFF", "IL_IDX", "PIV_OFF", "PIV_ROW", "PIV_COL", "PASSTHRU", "CAND_OFF", "OP_OFF", "OP"]
 SYMBOLS = ["nnca_build", "nnca_matvec", "nnca_matvec_host", "nnca_matvec_noalloc", "nnca_matvec_batch",
