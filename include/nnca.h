@@ -214,6 +214,24 @@ nnca_status nnca_matvec_noalloc(nnca_handle h, const void *x, void *y, int64_t l
 nnca_status nnca_matvec_batch(const nnca_handle *h, int count, const void *const *x, void *const *y,
                               const int64_t *ld, int64_t nrhs, int dtype, int precision, void *stream);
 
+/* Gradient of L = sum_r g_r^T A~ x_r with respect to the points and the kernel
+ * parameter h = kparam[1], with every index set of the build held (tree, lists,
+ * pivots t^{B,i}, s^{B,i}: "pivots fixed"); A~ moves with the points through its
+ * kernel entries and through the bases X_B = A_{t~ sigma} (A_{tau sigma})^{-1}
+ * (Sec. 2.3.1, Eqs. 11 and 14), differentiated as
+ * dX = (dA_{t~ sigma} - X dA_{tau sigma}) (A_{tau sigma})^{-1}. The derivative in x
+ * is A~ g (the product, A~ being symmetric).
+ *   x, g    device FP64, nrhs right-hand sides, column r at [r*ld .. r*ld + n),
+ *           caller's point order;
+ *   grad_p  device FP64, n x d row-major (grad_p[i*d + k]), caller's order;
+ *           overwritten;
+ *   grad_h  device FP64 [1] or NULL; dL/dh (0 for the log and 1/r kernels).
+ * Kernels: NNCA_K_LOG, NNCA_K_INV_R, NNCA_K_GAUSS, NNCA_K_MATERN (else
+ * NNCA_ERR_UNSUPPORTED). FP64 throughout (the products of x and g run in FP64).
+ * Synchronises `stream`; allocates scratch for the call. */
+nnca_status nnca_gradient(nnca_handle h, const double *x, const double *g, int64_t nrhs, int64_t ld, double *grad_p,
+                          double *grad_h, void *stream);
+
 /* Testing hook for the bounded waits of the FP32 product (the paper has no
  * counterpart; a failure-handling service). The FP32 M2L and near-field kernels
  * wait on shared-memory barriers of their own thread block for their own bulk

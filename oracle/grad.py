@@ -182,16 +182,22 @@ def h2_loss_gradient(h, x: np.ndarray, g: np.ndarray):
     return float(L), out, dh
 
 
-def dense_loss_gradient(P: np.ndarray, cfg, x: np.ndarray, g: np.ndarray):
-    """(L, dL/dP, dL/dh) of the dense L = g^T A x, A(i, j) = K(p_i, p_j), A(i, i) fixed."""
+def dense_loss_gradient(P: np.ndarray, cfg, x: np.ndarray, g: np.ndarray, rows_per_block: int = 256):
+    """(L, dL/dP, dL/dh) of the dense L = g^T A x, A(i, j) = K(p_i, p_j), A(i, i) fixed,
+    by blocks of rows (the same sums, bounded memory)."""
     P = np.asarray(P, dtype=np.float64)
-    K, gK, hK = radial_kernel_derivatives(cfg, P, P)
     n = P.shape[0]
-    idx = np.arange(n)
-    K[idx, idx] = cfg.kparam[2]
-    gK[idx, idx] = 0.0
-    hK[idx, idx] = 0.0
-    L = float(g @ K @ x)
-    wgt = g[:, None] * x[None, :] + x[:, None] * g[None, :]
-    grad = np.einsum("ij,ijk->ik", wgt, gK)
-    return L, grad, float(g @ hK @ x)
+    L, dh = 0.0, 0.0
+    grad = np.zeros_like(P)
+    for i0 in range(0, n, rows_per_block):
+        i1 = min(n, i0 + rows_per_block)
+        K, gK, hK = radial_kernel_derivatives(cfg, P[i0:i1], P)
+        idx = np.arange(i0, i1)
+        K[idx - i0, idx] = cfg.kparam[2]
+        gK[idx - i0, idx] = 0.0
+        hK[idx - i0, idx] = 0.0
+        L += float(g[i0:i1] @ K @ x)
+        wgt = g[i0:i1, None] * x[None, :] + x[i0:i1, None] * g[None, :]
+        grad[i0:i1] = np.einsum("ij,ijk->ik", wgt, gK)
+        dh += float(g[i0:i1] @ hK @ x)
+    return L, grad, dh

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnnca.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "tree.cu", "lists.cu", "aca.cu", "matvec.cu", "m2l_tc.cu", "scan.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "tree.cu", "lists.cu", "aca.cu", "matvec.cu", "m2l_tc.cu", "grad.cu", "scan.cu", "noalloc.cu"]
 HEADERS = ["nnca_internal.cuh", "dev_common.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

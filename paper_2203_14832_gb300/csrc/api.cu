@@ -361,6 +361,25 @@ nnca_status nnca_matvec_host(nnca_handle h, const void *x_host, void *y_host, in
     return NNCA_OK;
 }
 
+nnca_status nnca_gradient(nnca_handle h, const double *x, const double *g, int64_t nrhs, int64_t ld, double *grad_p,
+                          double *grad_h, void *stream) {
+    if (!h) return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_gradient: NULL handle");
+    if (!x || !g || !grad_p) return fail(h, NNCA_ERR_INVALID_ARG, "nnca_gradient: NULL x, g or grad_p");
+    if (nrhs < 1 || ld < h->n) return fail(h, NNCA_ERR_INVALID_ARG, "nnca_gradient: bad nrhs or ld");
+    if (!is_device_ptr(x) || !is_device_ptr(g) || !is_device_ptr(grad_p) || (grad_h && !is_device_ptr(grad_h)))
+        return fail(h, NNCA_ERR_INVALID_ARG, "nnca_gradient: x, g, grad_p and grad_h must be device memory");
+    try {
+        h->stream = (cudaStream_t)stream;
+        gradient(h, x, g, nrhs, ld, grad_p, grad_h);
+        NNCA_REQUIRE(!(read_status(h) & DEV_ZERO_PIVOT), NNCA_ERR_INTERNAL, "nnca_gradient: singular pivot block");
+    } catch (const Error &e) {
+        return fail(h, e.status, e.what());
+    } catch (const std::exception &e) {
+        return fail(h, NNCA_ERR_INTERNAL, e.what());
+    }
+    return NNCA_OK;
+}
+
 nnca_status nnca_set_wait_test(int64_t wait_limit_clocks, unsigned extra_tx_bytes) {
     try {
         set_wait_test(wait_limit_clocks, extra_tx_bytes);

@@ -391,6 +391,10 @@ void set_wait_test_tc(int64_t wait_limit_clocks, unsigned extra_tx_bytes);
 // Tensor-core M2L (m2l_tc.cu) of one pass of nr <= tc_rhs_per_pass() right-hand
 // sides: w and u right-hand-side major FP64 (nr rows of npiv); tcws holds
 // tc_workspace_floats(h) floats. mode: NNCA_PREC_TF32X3, NNCA_PREC_TF32 or NNCA_PREC_BF16.
+// Gradient of sum_r g_r^T A~ x_r in the points (caller order, n x d) and in
+// kparam[1], pivots fixed (grad.cu); x, g FP64 device, nrhs columns of ld.
+// Synchronises the handle's stream.
+void gradient(Handle *h, const double *x, const double *g, int64_t nrhs, int64_t ld, double *grad_p, double *grad_h);
 int tc_rhs_per_pass();
 size_t tc_workspace_floats(const Handle *h);
 void m2l_tensor(Handle *h, int mode, int nr, const double *w, double *u, float *tcws);

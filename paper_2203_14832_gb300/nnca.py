@@ -31,6 +31,7 @@ EXPORTS = ["PERM", "KEYS", "LEVEL_BASE", "CKEY", "CBEG", "CEND", "CPAR", "CCH_BE
            "IL_OFF", "IL_IDX", "PIV_OFF", "PIV_ROW", "PIV_COL", "PASSTHRU", "CAND_OFF", "OP_OFF", "OP"]
 SYMBOLS = ["nnca_build", "nnca_matvec", "nnca_matvec_host", "nnca_matvec_noalloc", "nnca_matvec_batch",
            "nnca_destroy", "nnca_get_stats", "nnca_export", "nnca_set_profiling", "nnca_set_wait_test",
+           "nnca_gradient",
            "nnca_last_error", "nnca_status_string"]
 
 
@@ -84,6 +85,8 @@ def lib() -> C.CDLL:
         L.nnca_matvec_batch.restype = C.c_int
         L.nnca_matvec_batch.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(C.c_int64),
                                         C.c_int64, C.c_int, C.c_int, vp]
+        L.nnca_gradient.restype = C.c_int
+        L.nnca_gradient.argtypes = [vp, vp, vp, C.c_int64, C.c_int64, vp, vp, vp]
         L.nnca_set_wait_test.restype = C.c_int
         L.nnca_set_wait_test.argtypes = [C.c_int64, C.c_uint]
         L.nnca_set_profiling.restype = C.c_int
@@ -185,6 +188,15 @@ def nnca_matvec_host(handle, x: np.ndarray, y: np.ndarray, nrhs: int, ld: int, p
     assert x.dtype == y.dtype and x.flags.c_contiguous and y.flags.c_contiguous
     _check(lib().nnca_matvec_host(handle, x.ctypes.data, y.ctypes.data, nrhs, ld, dtype, precision,
                                   _stream_ptr(stream)), handle)
+
+
+def nnca_gradient(handle, x, g, nrhs: int, ld: int, grad_p, grad_h=None, stream=None) -> None:
+    """dL/dP (into grad_p, n x d) and dL/dh (into grad_h, one element) of
+    L = sum_r g_r^T A~ x_r with the pivots fixed; all FP64 device tensors."""
+    import torch
+    assert x.dtype == g.dtype == grad_p.dtype == torch.float64 and x.is_cuda and g.is_cuda and grad_p.is_cuda
+    _check(lib().nnca_gradient(handle, x.data_ptr(), g.data_ptr(), nrhs, ld, grad_p.data_ptr(),
+                               grad_h.data_ptr() if grad_h is not None else None, _stream_ptr(stream)), handle)
 
 
 def nnca_set_wait_test(wait_limit_clocks: int, extra_tx_bytes: int) -> None:
