@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override N (not the benchmark workload)")
+    ap.add_argument("--leaf-size", type=int, default=0, help="override the workload's leaf size nu")
+    ap.add_argument("--tune", action="store_true",
+                    help="pick the leaf size by timing the product (batch.tune_leaf_size over 64, 128, 256)")
     ap.add_argument("--workload", default="invr3d_1m",
                     choices=["invr3d_1m", "sphere_512k", "gauss_mix_256k", "cheb2d_102k", "cheb3d_262k", "batch32",
                              "fredholm3d"],
@@ -254,6 +257,9 @@ def run_ours(args):
     w = W.WORKLOADS[WORKLOAD]
     if args.n:
         w = w.scaled(sample_size(w, args.n))
+    if args.leaf_size:
+        w = W.Workload(w.name, w.n, w.d, w.kernel, w.kparam, args.leaf_size, w.aca_tol, w.nrhs, w.seed, w.points,
+                       w.vector, w.note)
     # independent replicas: every rank draws its own instance of the recipe
     if rank:
         w = W.Workload(w.name, w.n, w.d, w.kernel, w.kparam, w.leaf_size, w.aca_tol, w.nrhs, w.seed + 17 * rank,
@@ -264,9 +270,17 @@ def run_ours(args):
     xh = w.make_vector()
     cfg = nnca.Config(d=w.d, leaf_size=w.leaf_size, aca_tol=w.aca_tol, kernel=w.kernel, kparam=w.kparam)
 
+    prec, dtype_label, form = PRECISIONS[args.precision]
+    leaf_times = None
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h = nnca.H2(P, cfg)
+    if args.tune:
+        from paper_2203_14832_gb300 import batch
+        h, leaf_times = batch.tune_leaf_size(P, cfg, torch.as_tensor(xh, device="cuda"), prec, (64, 128, 256))
+        w = W.Workload(w.name, w.n, w.d, w.kernel, w.kparam, h.cfg.leaf_size, w.aca_tol, w.nrhs, w.seed, w.points,
+                       w.vector, w.note)
+    else:
+        h = nnca.H2(P, cfg)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     st = h.stats()
@@ -274,7 +288,6 @@ def run_ours(args):
     x = torch.as_tensor(xh, device="cuda")
     y32 = torch.empty_like(x)
     y64 = torch.empty_like(x)
-    prec, dtype_label, form = PRECISIONS[args.precision]
     h.matvec(x, nnca.PREC_FP64, out=y64)
     h.matvec(x, prec, out=y32)
     torch.cuda.synchronize()
@@ -388,6 +401,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype_label, "data": "synthetic",
         "config": {"workload": workload_desc(w), "form": form,
+                   "leaf_size_tuning": {str(k): v for k, v in leaf_times.items()} if leaf_times else None,
                    "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas x{ws}"},
         "rel_err_fp32_vs_fp64": err32, "rel_err_fp64_vs_dense_256rows": err_dense,
         "rel_err_fp32_vs_dense_256rows": err_dense32,
@@ -455,6 +469,7 @@ def pass_rooflines(h, st, pass_ms, sms, sm_mhz, peaks, nr, precision="fp32"):
     # one RHS: the symmetric form evaluates each pivot pair once; passes of four: every
     # ordered pair once for the four
     evals = (st.get("m2l_evals") or st["m2l_pairs"]) if nr == 1 else st["m2l_pairs"]
+    grp = 8 if precision != "fp32" else 4   # right-hand sides per operator pass
     if precision != "fp32":
         # tensor-core M2L: useful flops of the contraction (2 per pivot pair and
         # right-hand side, times the products per pair), against the tf32 dense
@@ -474,9 +489,9 @@ def pass_rooflines(h, st, pass_ms, sms, sm_mhz, peaks, nr, precision="fp32"):
             "point pairs (evaluations)", pass_ms[4], FP32_PER_CLK_SM / NEAR_OPS_PER_PAIR * sms * clk,
             f"FP32 pipe at {NEAR_OPS_PER_PAIR} lane-ops per pair, one evaluation per pair and group of up to 4 "
             "right-hand sides; includes the FP64 L2P of the same kernel"),
-        ent("p2m_m2m", "k_upward", "hbm", 8 * (op_all * max(1, nr // 4) + nr * (n + npiv)), "bytes", pass_ms[1], hbm,
+        ent("p2m_m2m", "k_upward", "hbm", 8 * (op_all * max(1, nr // grp) + nr * (n + npiv)), "bytes", pass_ms[1], hbm,
             "FP64 operators of every cell + x in tree order + w; " + hbm_note),
-        ent("l2l", "k_l2l", "hbm", 8 * (op_nonleaf * max(1, nr // 4) + 2 * nr * npiv), "bytes", pass_ms[3], hbm,
+        ent("l2l", "k_l2l", "hbm", 8 * (op_nonleaf * max(1, nr // grp) + 2 * nr * npiv), "bytes", pass_ms[3], hbm,
             "FP64 translations of the non-leaf cells + u read and written; " + hbm_note),
     ]
     af = os.path.join(ROOT, "profiles", "aca_invr3d_131k.json")

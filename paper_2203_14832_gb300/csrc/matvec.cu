@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(UP_THREADS) k_upward(int64_t b0, int64_t b1, i
                                                       T *w, int64_t npiv, float *spk_w, const int32_t *spk_off,
                                                       float *spw = nullptr) {
     constexpr int TEAMS = UP_THREADS / (32 * TW);
-    constexpr int CH = TW == 1 ? 64 : UP_CHUNK;   // rows staged per chunk
+    // rows staged per chunk (halved for eight right-hand sides: the static shared memory)
+    constexpr int CH = (TW == 1 ? 64 : UP_CHUNK) / (NR > 4 ? 2 : 1);
     __shared__ T sv[TEAMS][NR][CH];
     __shared__ T part[TEAMS][TW][NR][32];
     const int lane = threadIdx.x & 31, tw = (threadIdx.x >> 5) % TW, team = threadIdx.x / (32 * TW);
@@ -2305,8 +2306,9 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
 
 // The tensor-core forms: passes of up to tc_rhs_per_pass() right-hand sides.
 // Per pass: the permutation and the upward pass for all of its right-hand
-// sides (groups of M2L_RHS, FP64 operators), one tensor-core M2L for all of
-// them, then L2L and the near field (the FP32 kernels) group by group.
+// sides (groups of eight, FP64 operators: each operator load serves eight),
+// one tensor-core M2L for all of them, then L2L (groups of eight) and the near
+// field (the FP32 kernels, groups of M2L_RHS).
 template <int KIND, class TO>
 void run_tc(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int mode) {
     cudaStream_t s = h->stream;
@@ -2335,7 +2337,10 @@ void run_tc(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int mod
         const bool far = h->lmin <= h->kappa && npiv > 0;
         if (far) {
             for (int r = 0; r < nr;) {
-                if (nr - r >= M2L_RHS) {
+                if (nr - r >= 2 * M2L_RHS) {
+                    pass_up<2 * M2L_RHS>(h, xt + r * N, w + r * npiv, nullptr, nullptr);
+                    r += 2 * M2L_RHS;
+                } else if (nr - r >= M2L_RHS) {
                     pass_up<M2L_RHS>(h, xt + r * N, w + r * npiv, nullptr, nullptr);
                     r += M2L_RHS;
                 } else {
@@ -2350,7 +2355,10 @@ void run_tc(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int mod
         prof_mark(h, 3);
         if (far)
             for (int r = 0; r < nr;) {
-                if (nr - r >= M2L_RHS) {
+                if (nr - r >= 2 * M2L_RHS) {
+                    pass_l2l<2 * M2L_RHS>(h, u + r * npiv);
+                    r += 2 * M2L_RHS;
+                } else if (nr - r >= M2L_RHS) {
                     pass_l2l<M2L_RHS>(h, u + r * npiv);
                     r += M2L_RHS;
                 } else {
