@@ -72,8 +72,8 @@ def parse():
     ap.add_argument("--tune", action="store_true",
                     help="pick the leaf size by timing the product (batch.tune_leaf_size over 64, 128, 256)")
     ap.add_argument("--workload", default="invr3d_1m",
-                    choices=["invr3d_1m", "sphere_512k", "gauss_mix_256k", "cheb2d_102k", "cheb3d_262k", "batch32",
-                             "fredholm3d"],
+                    choices=["invr3d_1m", "log2d_4096", "sphere_512k", "gauss_mix_256k", "cheb2d_102k", "cheb3d_262k",
+                             "batch32", "fredholm3d"],
                     help="the headline is invr3d_1m; batch32: 32 independent problems in one captured graph; "
                          "fredholm3d: GMRES on the Nystrom system of the second-kind equation")
     ap.add_argument("--no-tune", action="store_true", help="batch32: keep leaf size 64 instead of tuning it")
@@ -355,7 +355,9 @@ def run_ours(args):
     # dense check on sampled rows (FP64 oracle dense product, host cores)
     from oracle import oracle as O
     ocfg = O.Config(d=w.d, leaf_size=w.leaf_size, aca_tol=w.aca_tol, kernel=w.kernel, kparam=w.kparam)
-    rows = np.random.default_rng(12345).choice(N, 256, replace=False)
+    # every row for small problems, else 4096 sampled rows
+    nrows = N if N <= 16384 else 4096
+    rows = np.arange(N) if nrows == N else np.random.default_rng(12345).choice(N, nrows, replace=False)
     os.environ.setdefault("OMP_NUM_THREADS", str(host_cores()))
     x0 = xh if xh.ndim == 1 else xh[0]       # the dense check takes the first right-hand side
     y64f = y64h if y64h.ndim == 1 else y64h[0]
@@ -403,8 +405,8 @@ def run_ours(args):
         "config": {"workload": workload_desc(w), "form": form,
                    "leaf_size_tuning": {str(k): v for k, v in leaf_times.items()} if leaf_times else None,
                    "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas x{ws}"},
-        "rel_err_fp32_vs_fp64": err32, "rel_err_fp64_vs_dense_256rows": err_dense,
-        "rel_err_fp32_vs_dense_256rows": err_dense32,
+        "rel_err_fp32_vs_fp64": err32, "rel_err_fp64_vs_dense": err_dense,
+        "rel_err_fp32_vs_dense": err_dense32, "dense_rows": int(nrows),
         "fp64_form": {"value": N * nrhs / (fp64_ms / 1e3), "unit": "points/s", "ms_per_step": fp64_ms},
         "speedup_fp32_vs_fp64": fp64_ms / (total_ms / args.steps),
         "build": {"s": build_s, "ms_phases": st["build_ms"][:6], "kappa": st["kappa"], "lmin": st["lmin"],
@@ -523,7 +525,8 @@ def run_batch(args):
         probs.append(batch.Problem(P, cfg, torch.as_tensor(np.ascontiguousarray(w.make_vector()), device="cuda")))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    b = batch.Batch(probs, precision=nnca.PREC_FP32, tune=not args.no_tune)
+    prec, dtype_label, form = PRECISIONS[args.precision]
+    b = batch.Batch(probs, precision=prec, tune=not args.no_tune)
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     # per-problem error of the FP32 form against the FP64 form of the same handle
@@ -579,9 +582,10 @@ def run_batch(args):
     peak_gpair = MUFU_PER_CLK_SM * sms * sm_max * 1e6 / 1e9
     achieved = m2l_pairs * b.nrhs / (total_ms / args.steps / 1e3) / 1e9
     out = {
-        "metric": "batched H2 matvec points/s, 32 uneven problems, FP32 form", "value": value, "unit": "points/s",
-        "n_gpus": ws_, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "metric": f"batched H2 matvec points/s, 32 uneven problems, {args.precision} form", "value": value,
+        "unit": "points/s", "n_gpus": ws_, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": dtype_label, "data": "synthetic", "form": form,
         "config": {"workload": "batch32: 32 problems, N log-uniform in [16384, 524288], U[0,1]^3, 16x 1/r + 16x "
                                "Gaussian h=0.2, ACA tol 1e-6, 8 RHS", "sizes": [h.n for h in b.handles],
                    "leaf_sizes": [h.cfg.leaf_size for h in b.handles], "tuned": not args.no_tune,
