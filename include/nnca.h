@@ -115,7 +115,11 @@ typedef struct {
                           pair evaluated once, for both u_B and u_B'; ranks up
                           to 256), NNCA_M2L_FULL always the full form (each target sums
                           its whole interaction list)                            */
-    int reserved[2];   /* set to 0                                                */
+    int m2l_item_targets; /* tile of the FP32 M2L: targets (pivots of one parent's
+                          children) per work item, 32..256, or 0 for 256; a
+                          tuning parameter (it changes only the order of the
+                          FP32 partial sums)                                   */
+    int reserved;      /* set to 0                                                */
 } nnca_config;
 
 /* Sizes and timings of a built handle (the quantities of the paper's

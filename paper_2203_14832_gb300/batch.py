@@ -13,6 +13,7 @@ from dataclasses import dataclass
 from . import nnca
 
 LEAF_CANDIDATES = (32, 64, 96, 128)
+TILE_CANDIDATES = (0, 128)   # M2L targets per work item (0: 256)
 
 
 def time_product(h: "nnca.H2", x, y, precision: int, reps: int = 5) -> float:
@@ -30,24 +31,44 @@ def time_product(h: "nnca.H2", x, y, precision: int, reps: int = 5) -> float:
 
 
 def tune_leaf_size(P, cfg: "nnca.Config", x, precision: int = nnca.PREC_FP32,
-                   candidates=LEAF_CANDIDATES, reps: int = 5):
-    """Build the problem with every candidate leaf size, time its product on x, and
-    keep the fastest. Returns (handle of the best leaf size, {leaf size: ms})."""
+                   candidates=LEAF_CANDIDATES, reps: int = 5, tiles=TILE_CANDIDATES):
+    """Pick the leaf size and then the M2L tile (targets per work item) by timing.
+
+    Every candidate leaf size is built (default tile) and its product timed on x;
+    with the fastest one kept, every tile of `tiles` is built and timed. Returns
+    (handle of the best configuration, {"nu/tile": ms})."""
     import torch
-    best, times = None, {}
     y = torch.empty_like(x)
-    for nu in candidates:
+    times = {}
+
+    def build(nu, tile):
         c = nnca.Config(d=cfg.d, leaf_size=nu, eta2_num=cfg.eta2_num, eta2_den=cfg.eta2_den, aca_tol=cfg.aca_tol,
-                        kernel=cfg.kernel, kparam=cfg.kparam)
-        h = nnca.H2(P, c)
-        times[nu] = time_product(h, x, y, precision, reps)
-        if best is None or times[nu] < times[best[0]]:
+                        kernel=cfg.kernel, kparam=cfg.kparam, m2l_form=cfg.m2l_form, m2l_item_targets=tile)
+        return nnca.H2(P, c)
+
+    best = None   # (ms, nu, tile, handle)
+    for nu in candidates:
+        h = build(nu, 0)
+        t = time_product(h, x, y, precision, reps)
+        times[f"{nu}/0"] = t
+        if best is None or t < best[0]:
             if best is not None:
-                best[1].close()
-            best = (nu, h)
+                best[3].close()
+            best = (t, nu, 0, h)
         else:
             h.close()
-    return best[1], times
+    for tile in tiles:
+        if tile == 0:
+            continue
+        h = build(best[1], tile)
+        t = time_product(h, x, y, precision, reps)
+        times[f"{best[1]}/{tile}"] = t
+        if t < best[0]:
+            best[3].close()
+            best = (t, best[1], tile, h)
+        else:
+            h.close()
+    return best[3], times
 
 
 @dataclass
@@ -60,7 +81,7 @@ class Problem:
 class Batch:
     """A set of independent problems with one batched product.
 
-    tune=True picks each problem's leaf size with ``tune_leaf_size``."""
+    tune=True picks each problem's leaf size and M2L tile with ``tune_leaf_size``."""
 
     def __init__(self, problems: list, precision: int = nnca.PREC_FP32, tune: bool = False,
                  candidates=LEAF_CANDIDATES):

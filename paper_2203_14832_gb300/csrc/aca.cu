@@ -1241,6 +1241,7 @@ void build_finish(Handle *h) {
         NNCA_CUDA(cudaMemcpy(hchb.data(), h->cch_beg, nc * sizeof(int32_t), cudaMemcpyDeviceToHost));
         NNCA_CUDA(cudaMemcpy(hche.data(), h->cch_end, nc * sizeof(int32_t), cudaMemcpyDeviceToHost));
         struct Group { int64_t weight; int parent_slot, t0, nt; };
+        const int item_targets = h->cfg.m2l_item_targets > 0 ? h->cfg.m2l_item_targets : M2L_GROUP_TARGETS;
         std::vector<Group> groups;
         std::vector<int32_t> parents;
         const int64_t pl0 = h->lmin >= 1 ? h->level_base[h->lmin - 1] : 0;
@@ -1258,8 +1259,8 @@ void build_finish(Handle *h) {
             }
             const int slot = (int)parents.size();
             parents.push_back((int32_t)P);
-            for (int64_t t0 = 0; t0 < T; t0 += M2L_GROUP_TARGETS) {
-                const int64_t t1 = std::min<int64_t>(T, t0 + M2L_GROUP_TARGETS);
+            for (int64_t t0 = 0; t0 < T; t0 += item_targets) {
+                const int64_t t1 = std::min<int64_t>(T, t0 + item_targets);
                 groups.push_back({work * (t1 - t0) / T, slot, (int)t0, (int)(t1 - t0)});
             }
         }
@@ -1300,6 +1301,7 @@ void build_finish(Handle *h) {
         struct Round { int k, n; int64_t src; };
         struct ItemSet {
             std::vector<int4> items;
+            std::vector<int64_t> weight;   // pairs (targets x staged sources) of each item
             std::vector<int> part;
             std::vector<int4> splits;
             int nparts = 0;
@@ -1357,6 +1359,7 @@ void build_finish(Handle *h) {
                              [](const Piece &x, const Piece &y) { return x.weight > y.weight; });
             for (auto &p : pieces) {
                 out.items.push_back(p.item);
+                out.weight.push_back(p.weight);
                 out.part.push_back(p.part);
             }
         };
@@ -1369,6 +1372,7 @@ void build_finish(Handle *h) {
             make_items(h->m2l_plan, h->n_m2l_plan, roff, false, hplan, full);
         }
         h->n_m2l_groups = (int)full.items.size();
+        h->h_m2l_weight = full.weight;
         h->m2l_groups = dalloc<int4>(h, full.items.size());
         h->m2l_item_part = dalloc<int>(h, full.part.size());
         h->m2l_next = dalloc<int>(h, 1);

@@ -2,6 +2,7 @@
 // export of internal arrays, and the host-buffer product. Every entry point
 // catches the library's internal errors and returns a status code.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -157,11 +158,15 @@ nnca_status nnca_build(const nnca_config *cfg, const double *P, int64_t nP, cons
         return fail(nullptr, NNCA_ERR_UNSUPPORTED, "nnca_build: only the symmetric form (P = Q, symmetric K) is built");
     if (cfg->m2l_form != NNCA_M2L_AUTO && cfg->m2l_form != NNCA_M2L_FULL)
         return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_build: unknown m2l_form");
+    if (cfg->m2l_item_targets != 0 && (cfg->m2l_item_targets < 32 || cfg->m2l_item_targets > 256))
+        return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_build: m2l_item_targets must be 0 or 32..256");
     if (Q && (Q != P || nQ != nP))
         return fail(nullptr, NNCA_ERR_UNSUPPORTED, "nnca_build: P != Q is not supported (pass Q = NULL or Q = P)");
     if (!is_device_ptr(P)) return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_build: P is not device memory");
 
+    static std::atomic<uint64_t> next_uid{1};
     nnca_handle_s *h = new nnca_handle_s();
+    h->uid = next_uid++;
     const auto t0 = std::chrono::steady_clock::now();
     try {
         h->cfg = *cfg;
@@ -309,6 +314,12 @@ nnca_status nnca_matvec_batch(const nnca_handle *hs, int count, const void *cons
         BatchPool &P = batch_pool();
         const cudaStream_t s = (cudaStream_t)stream;
         const int nw = std::min(count, kBatchStreams);
+        if (precision == NNCA_PREC_FP32 &&
+            matvec_batch_fp32(reinterpret_cast<Handle *const *>(hs), count, x, y, ld, nrhs, dtype, s, P.s, nw, P.fork,
+                              P.join)) {
+            for (k = 0; k < count; ++k) hs[k]->stats.launches_per_product = hs[k]->launches;
+            return NNCA_OK;
+        }
         NNCA_CUDA(cudaEventRecord(P.fork, s));
         for (int i = 0; i < nw; ++i) NNCA_CUDA(cudaStreamWaitEvent(P.s[i], P.fork, 0));
         for (k = 0; k < count; ++k) {

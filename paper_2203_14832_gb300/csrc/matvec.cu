@@ -24,6 +24,8 @@
 //
 // Vectors in tree order are right-hand-side major: x_t[r * N + i].
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "nnca_internal.cuh"
 
@@ -1565,16 +1567,32 @@ __device__ __forceinline__ int m2l_stage_rhs(M2lRhsSmem &S, int b, unsigned use,
 }
 
 
-template <int KIND>
-__global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group_rhs(KParams kp, const int4 *items, int nitems,
-                                                                   int *next_item, const int4 *plan,
-                                                                   const float4 *plan_sh, const int32_t *cch_beg,
-                                                                   const int32_t *cch_end, const int2 *prange,
-                                                                   const float4 *pv4, const float4 *chi,
-                                                                   const float4 *clo, const float4 *spk,
-                                                                   const float4 *spw, const int *item_part,
-                                                                   double *parts, double *u, int64_t npiv,
-                                                                   unsigned *status) {
+// The arguments of one problem of the four-RHS FP32 M2L. A launch serves the
+// problems of a table, passed by value as a __grid_constant__ parameter (no
+// device memory to fill, and captured as it is by a CUDA graph): items come from
+// one counter over a cross-problem list of (problem, item) pairs, heaviest
+// first, or, without such a list, from the first problem's own items.
+struct M2lRhsArgs {
+    KParams kp;
+    const int4 *items;
+    const int4 *plan;
+    const float4 *plan_sh;
+    const int32_t *cch_beg, *cch_end;
+    const int2 *prange;
+    const float4 *pv4, *chi, *clo, *spk, *spw;
+    const int *item_part;
+    double *parts, *u;
+    int64_t npiv;
+    unsigned *status;
+};
+template <int NT> struct M2lRhsTable {
+    M2lRhsArgs a[NT];
+};
+constexpr int M2L_MULTI_MAX = 48;   // problems of one cross-problem launch (the table is a kernel parameter)
+
+template <int KIND, int NT>
+__global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group_rhs(const __grid_constant__ M2lRhsTable<NT> tab,
+                                                                   const int2 *gitems, int nitems, int *next_item) {
     extern __shared__ __align__(128) unsigned char m2l_rhs_smem[];
     M2lRhsSmem &S = *reinterpret_cast<M2lRhsSmem *>(m2l_rhs_smem);
     const int tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
@@ -1592,10 +1610,25 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group_rhs(KParams kp,
         __syncthreads();
         if (tid == 0) S.item = atomicAdd(next_item, 1);
         __syncthreads();
-        const int it = S.item;
-        if (it >= nitems || *(volatile int *)&S.abort) break;
-        const int4 item = items[it];
-        const int part = item_part[it];
+        const int gi = S.item;
+        if (gi >= nitems || *(volatile int *)&S.abort) break;
+        int pidx = 0, it = gi;
+        if (gitems) {
+            const int2 e = gitems[gi];
+            pidx = e.x;
+            it = e.y;
+        }
+        const M2lRhsArgs &A = tab.a[pidx];
+        const KParams &kp = A.kp;
+        const int4 *plan = A.plan;
+        const float4 *plan_sh = A.plan_sh, *pv4 = A.pv4, *chi = A.chi, *clo = A.clo, *spk = A.spk, *spw = A.spw;
+        const int32_t *cch_beg = A.cch_beg, *cch_end = A.cch_end;
+        const int2 *prange = A.prange;
+        double *parts = A.parts, *u = A.u;
+        const int64_t npiv = A.npiv;
+        unsigned *status = A.status;
+        const int4 item = A.items[it];
+        const int part = A.item_part[it];
         const int P = item.x, t0 = item.y & 0xffff, nt = item.y >> 16, kend = item.z + item.w;
         const int cb = cch_beg[P], nch = cch_end[P] - cb;
         if (tid < nch) S.ch_range[tid] = prange[cb + tid];
@@ -2055,28 +2088,61 @@ void launch_m2l_sym(Handle *h, const double *w, double *u) {
 }
 
 // M2L_RHS right-hand sides at once (u: M2L_RHS rows of npiv)
-template <int KIND>
-void launch_m2l_f32_rhs(Handle *h, double *u) {
-    if (!h->n_m2l_groups) return;
+M2lRhsArgs m2l_rhs_args(Handle *h, double *u) {
+    M2lRhsArgs A{};
+    A.kp = h->kp;
+    A.items = h->m2l_groups;
+    A.plan = h->m2l_plan;
+    A.plan_sh = h->m2l_plan_sh;
+    A.cch_beg = h->cch_beg;
+    A.cch_end = h->cch_end;
+    A.prange = h->prange;
+    A.pv4 = h->pv4;
+    A.chi = h->chi4;
+    A.clo = h->clo4;
+    A.spk = h->spk;
+    A.spw = h->spw;
+    A.item_part = h->m2l_item_part;
+    A.parts = h->m2l_parts;
+    A.u = u;
+    A.npiv = h->npiv;
+    A.status = h->dev_status;
+    return A;
+}
+
+// one launch of the four-RHS FP32 M2L over a table of problems (gitems: the
+// cross-problem (problem, item) list, or null for the first problem's items)
+template <int KIND, int NT>
+void launch_m2l_rhs_table(const M2lRhsTable<NT> &tab, const int2 *gitems, int nitems, int *next, cudaStream_t s) {
     const int smem = (int)sizeof(M2lRhsSmem);
-    NNCA_CUDA(cudaFuncSetAttribute(k_m2l_group_rhs<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    NNCA_CUDA(cudaFuncSetAttribute(k_m2l_group_rhs<KIND, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int dev = 0, nsm = 152, per_sm = 1;
     NNCA_CUDA(cudaGetDevice(&dev));
     NNCA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    NNCA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_m2l_group_rhs<KIND>, M2L_GROUP_THREADS, smem));
-    const unsigned g = (unsigned)std::min<int64_t>(h->n_m2l_groups, (int64_t)nsm * std::max(1, per_sm));
-    NNCA_CUDA(cudaMemsetAsync(h->m2l_next, 0, sizeof(int), h->stream));
-    k_m2l_group_rhs<KIND><<<g, M2L_GROUP_THREADS, smem, h->stream>>>(
-        h->kp, h->m2l_groups, h->n_m2l_groups, h->m2l_next, h->m2l_plan, h->m2l_plan_sh, h->cch_beg, h->cch_end,
-        h->prange, h->pv4, h->chi4, h->clo4, h->spk, h->spw, h->m2l_item_part, h->m2l_parts, u, h->npiv, h->dev_status);
+    NNCA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_m2l_group_rhs<KIND, NT>, M2L_GROUP_THREADS, smem));
+    const unsigned g = (unsigned)std::min<int64_t>(nitems, (int64_t)nsm * std::max(1, per_sm));
+    NNCA_CUDA(cudaMemsetAsync(next, 0, sizeof(int), s));
+    k_m2l_group_rhs<KIND, NT><<<g, M2L_GROUP_THREADS, smem, s>>>(tab, gitems, nitems, next);
+    NNCA_LAUNCH_CHECK();
+}
+
+void m2l_rhs_combine(Handle *h, double *u) {
+    if (!h->n_m2l_split) return;
+    k_m2l_combine<<<(unsigned)std::min(h->n_m2l_split, 152 * 16), 256, 0, h->stream>>>(h->m2l_split, h->n_m2l_split,
+                                                                                       h->m2l_parts, u, M2L_RHS,
+                                                                                       h->npiv);
     NNCA_LAUNCH_CHECK();
     ++h->launches;
-    if (h->n_m2l_split) {
-        k_m2l_combine<<<(unsigned)std::min(h->n_m2l_split, 152 * 16), 256, 0, h->stream>>>(
-            h->m2l_split, h->n_m2l_split, h->m2l_parts, u, M2L_RHS, h->npiv);
-        NNCA_LAUNCH_CHECK();
-        ++h->launches;
-    }
+}
+
+template <int KIND>
+void launch_m2l_f32_rhs(Handle *h, double *u) {
+    if (!h->n_m2l_groups) return;
+    M2lRhsTable<1> tab;
+    tab.a[0] = m2l_rhs_args(h, u);
+    launch_m2l_rhs_table<KIND, 1>(tab, nullptr, h->n_m2l_groups, h->m2l_next, h->stream);
+    ++h->launches;
+    m2l_rhs_combine(h, u);
 }
 
 template <int KIND, class TO>
@@ -2437,6 +2503,168 @@ void set_wait_test(int64_t wait_limit_clocks, unsigned extra_tx_bytes) {
     NNCA_CUDA(cudaDeviceSynchronize());
 }
 
+// ---- batched products of independent problems (FP32 form) -------------------------
+// Cross-problem item lists of the four-RHS M2L, one per kernel family and group
+// of at most M2L_MULTI_MAX problems: (problem in the group, item) pairs, heaviest
+// first over all the group's problems. Built on the first call with a set of
+// handles and kept (a CUDA graph of the batched product refers to them).
+struct CrossList {
+    int kind = 0;
+    std::vector<int> members;   // indices into the call's handle array
+    int2 *gitems = nullptr;
+    int nitems = 0;
+    int *next = nullptr;
+};
+struct CrossPlan {
+    std::vector<CrossList> lists;
+};
+std::mutex g_cross_mutex;
+std::map<std::vector<uint64_t>, CrossPlan> g_cross_plans;
+
+CrossPlan &cross_plan(Handle *const *hs, int count) {
+    std::vector<uint64_t> key;
+    for (int k = 0; k < count; ++k) {
+        key.push_back(hs[k]->uid);
+        key.push_back((uint64_t)(uintptr_t)hs[k]);
+    }
+    std::lock_guard<std::mutex> lock(g_cross_mutex);
+    auto it = g_cross_plans.find(key);
+    if (it != g_cross_plans.end()) return it->second;
+    CrossPlan plan;
+    std::map<int, std::vector<int>> by_kind;
+    for (int k = 0; k < count; ++k)
+        if (hs[k]->n_m2l_groups > 0) by_kind[hs[k]->kp.kind].push_back(k);
+    for (auto &kv : by_kind)
+        for (size_t g0 = 0; g0 < kv.second.size(); g0 += M2L_MULTI_MAX) {
+            CrossList L;
+            L.kind = kv.first;
+            L.members.assign(kv.second.begin() + g0,
+                             kv.second.begin() + std::min(kv.second.size(), g0 + (size_t)M2L_MULTI_MAX));
+            std::vector<std::pair<int64_t, int2>> all;
+            for (size_t m = 0; m < L.members.size(); ++m) {
+                const Handle *h = hs[L.members[m]];
+                for (int i = 0; i < h->n_m2l_groups; ++i)
+                    all.push_back({i < (int)h->h_m2l_weight.size() ? h->h_m2l_weight[i] : 0, make_int2((int)m, i)});
+            }
+            std::stable_sort(all.begin(), all.end(), [](const std::pair<int64_t, int2> &a,
+                                                        const std::pair<int64_t, int2> &b) { return a.first > b.first; });
+            std::vector<int2> gi(all.size());
+            for (size_t i = 0; i < all.size(); ++i) gi[i] = all[i].second;
+            L.nitems = (int)gi.size();
+            NNCA_CUDA(cudaMalloc(&L.gitems, sizeof(int2) * std::max<size_t>(1, gi.size())));
+            NNCA_CUDA(cudaMalloc(&L.next, sizeof(int)));
+            if (!gi.empty())
+                NNCA_CUDA(cudaMemcpy(L.gitems, gi.data(), gi.size() * sizeof(int2), cudaMemcpyHostToDevice));
+            plan.lists.push_back(L);
+        }
+    return g_cross_plans.emplace(key, std::move(plan)).first->second;
+}
+
+template <int KIND>
+void launch_cross(Handle *const *hs, const CrossList &L, double *const *u, cudaStream_t s) {
+    M2lRhsTable<M2L_MULTI_MAX> tab;
+    for (size_t m = 0; m < L.members.size(); ++m) tab.a[m] = m2l_rhs_args(hs[L.members[m]], u[L.members[m]]);
+    launch_m2l_rhs_table<KIND, M2L_MULTI_MAX>(tab, L.gitems, L.nitems, L.next, s);
+}
+
+template <class TO>
+void near4_kind(Handle *h, const double *u, const double *xt, const float *xt32, TO *yout, int64_t ld) {
+    switch (h->kp.kind) {
+    case NNCA_K_INV_R: pass_near<true, M2L_RHS, NNCA_K_INV_R, TO>(h, u, xt, xt32, yout, ld); break;
+    case NNCA_K_LOG: pass_near<true, M2L_RHS, NNCA_K_LOG, TO>(h, u, xt, xt32, yout, ld); break;
+    case NNCA_K_GAUSS: pass_near<true, M2L_RHS, NNCA_K_GAUSS, TO>(h, u, xt, xt32, yout, ld); break;
+    case NNCA_K_MATERN: pass_near<true, M2L_RHS, NNCA_K_MATERN, TO>(h, u, xt, xt32, yout, ld); break;
+    case NNCA_K_PAPER_I: pass_near<true, M2L_RHS, NNCA_K_PAPER_I, TO>(h, u, xt, xt32, yout, ld); break;
+    default: pass_near<true, M2L_RHS, NNCA_K_PAPER_II, TO>(h, u, xt, xt32, yout, ld); break;
+    }
+}
+
+template <class TO>
+void batch_fp32(Handle *const *hs, int count, const void *const *x, void *const *y, const int64_t *ld, int64_t nrhs,
+                cudaStream_t s, cudaStream_t *wk, int nw, cudaEvent_t fork, cudaEvent_t *join) {
+    auto fork_all = [&]() {
+        NNCA_CUDA(cudaEventRecord(fork, s));
+        for (int i = 0; i < nw; ++i) NNCA_CUDA(cudaStreamWaitEvent(wk[i], fork, 0));
+    };
+    auto join_all = [&]() {
+        for (int i = 0; i < nw; ++i) {
+            NNCA_CUDA(cudaEventRecord(join[i], wk[i]));
+            NNCA_CUDA(cudaStreamWaitEvent(s, join[i], 0));
+        }
+    };
+    for (int k = 0; k < count; ++k) {
+        ensure_workspace(hs[k], std::min<int64_t>(nrhs, 4));
+        hs[k]->launches = 0;
+    }
+    CrossPlan &plan = cross_plan(hs, count);
+    std::vector<double *> uptr(count);
+    int64_t r0 = 0;
+    while (r0 < nrhs) {
+        if (nrhs - r0 < M2L_RHS) {
+            // a last right-hand side: the products of one right-hand side, problem by problem
+            fork_all();
+            for (int k = 0; k < count; ++k) {
+                Handle *h = hs[k];
+                h->stream = wk[k % nw];
+                switch (h->kp.kind) {
+                case NNCA_K_INV_R: run_chunk<true, 1, NNCA_K_INV_R, TO>(h, x[k], y[k], ld[k], r0); break;
+                case NNCA_K_LOG: run_chunk<true, 1, NNCA_K_LOG, TO>(h, x[k], y[k], ld[k], r0); break;
+                case NNCA_K_GAUSS: run_chunk<true, 1, NNCA_K_GAUSS, TO>(h, x[k], y[k], ld[k], r0); break;
+                case NNCA_K_MATERN: run_chunk<true, 1, NNCA_K_MATERN, TO>(h, x[k], y[k], ld[k], r0); break;
+                case NNCA_K_PAPER_I: run_chunk<true, 1, NNCA_K_PAPER_I, TO>(h, x[k], y[k], ld[k], r0); break;
+                default: run_chunk<true, 1, NNCA_K_PAPER_II, TO>(h, x[k], y[k], ld[k], r0); break;
+                }
+            }
+            join_all();
+            r0 += 1;
+            continue;
+        }
+        // permutation, P2M and M2M of every problem
+        fork_all();
+        for (int k = 0; k < count; ++k) {
+            Handle *h = hs[k];
+            h->stream = wk[k % nw];
+            const int64_t N = h->n, npiv = h->npiv;
+            double *xt = (double *)h->ws, *w = xt + M2L_RHS * N, *u = w + M2L_RHS * npiv;
+            float *xt32 = (float *)(u + M2L_RHS * npiv);
+            uptr[k] = u;
+            pass_perm<M2L_RHS, TO>(h, (const TO *)x[k] + r0 * ld[k], ld[k], xt, xt32, false);
+            if (npiv > 0) NNCA_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * M2L_RHS * npiv, h->stream));
+            if (h->lmin <= h->kappa && npiv > 0) pass_up<M2L_RHS>(h, xt, w, nullptr, reinterpret_cast<float *>(h->spw));
+        }
+        join_all();
+        // the M2L of all problems: one launch per kernel family over the cross-problem list
+        for (const CrossList &L : plan.lists) {
+            switch (L.kind) {
+            case NNCA_K_INV_R: launch_cross<NNCA_K_INV_R>(hs, L, uptr.data(), s); break;
+            case NNCA_K_LOG: launch_cross<NNCA_K_LOG>(hs, L, uptr.data(), s); break;
+            case NNCA_K_GAUSS: launch_cross<NNCA_K_GAUSS>(hs, L, uptr.data(), s); break;
+            case NNCA_K_MATERN: launch_cross<NNCA_K_MATERN>(hs, L, uptr.data(), s); break;
+            case NNCA_K_PAPER_I: launch_cross<NNCA_K_PAPER_I>(hs, L, uptr.data(), s); break;
+            default: launch_cross<NNCA_K_PAPER_II>(hs, L, uptr.data(), s); break;
+            }
+            ++hs[L.members[0]]->launches;
+        }
+        // split pieces, L2L and the near field of every problem
+        fork_all();
+        for (int k = 0; k < count; ++k) {
+            Handle *h = hs[k];
+            h->stream = wk[k % nw];
+            const int64_t N = h->n, npiv = h->npiv;
+            double *xt = (double *)h->ws, *u = uptr[k];
+            float *xt32 = (float *)(u + M2L_RHS * npiv);
+            if (h->lmin <= h->kappa && npiv > 0) {
+                m2l_rhs_combine(h, u);
+                pass_l2l<M2L_RHS>(h, u);
+            }
+            near4_kind<TO>(h, u, xt, xt32, (TO *)y[k] + r0 * ld[k], ld[k]);
+            (void)N;
+        }
+        join_all();
+        r0 += M2L_RHS;
+    }
+}
+
 template <class TO>
 void dispatch_tc(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int mode) {
     switch (h->kp.kind) {
@@ -2448,6 +2676,19 @@ void dispatch_tc(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, in
     case NNCA_K_PAPER_II: run_tc<NNCA_K_PAPER_II, TO>(h, x, y, nrhs, ld, mode); break;
     default: NNCA_REQUIRE(false, NNCA_ERR_UNSUPPORTED, "the tensor-core forms need a radial kernel");
     }
+}
+
+bool matvec_batch_fp32(Handle *const *hs, int count, const void *const *x, void *const *y, const int64_t *ld,
+                       int64_t nrhs, int dtype, cudaStream_t s, cudaStream_t *workers, int nworkers, cudaEvent_t fork,
+                       cudaEvent_t *join) {
+    if (nrhs < M2L_RHS) return false;
+    for (int k = 0; k < count; ++k) {
+        const Handle *h = hs[k];
+        if (!kernel_is_radial(h->kp.kind) || h->d > 3 || h->m2l_fp32_unsupported) return false;
+    }
+    if (dtype == NNCA_F64) batch_fp32<double>(hs, count, x, y, ld, nrhs, s, workers, nworkers, fork, join);
+    else batch_fp32<float>(hs, count, x, y, ld, nrhs, s, workers, nworkers, fork, join);
+    return true;
 }
 
 void matvec(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int dtype, int precision) {

@@ -235,6 +235,7 @@ struct Scratch {
 struct Handle {
     nnca_config cfg{};
     KParams kp{};
+    uint64_t uid = 0;                 // unique per built handle (keys of cross-problem caches)
     int d = 0, lmax = 0, kappa = 0, lmin = 0;
     int64_t n = 0;
     double corner[4] = {0, 0, 0, 0};
@@ -287,6 +288,7 @@ struct Handle {
     // (the products write the weights w), from pair spk_off[cell]
     int4 *m2l_groups = nullptr;
     int n_m2l_groups = 0;
+    std::vector<int64_t> h_m2l_weight;   // host: pairs of each item (cross-problem ordering)
     int *m2l_next = nullptr;      // item counter of the FP32 M2L launch
     // heavy items are split at staging-round boundaries: such a piece writes
     // its partial sums to m2l_parts[slot][0, targets), and a combine pass adds the
@@ -385,6 +387,14 @@ void build_lists(Handle *h);
 void build_pivots(Handle *h);   // pivots, bases, global pivot/operator arrays
 void build_finish(Handle *h);   // data of the product: centres, FP32 coordinates, work lists
 void matvec(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int dtype, int precision);
+// Batched FP32 products of independent handles (matvec.cu): passes of four
+// right-hand sides synchronised across the problems, the M2L of each pass one
+// launch per kernel family over a cross-problem item list; the other passes per
+// problem on the worker streams. Returns false (and does nothing) if a handle
+// cannot take this path.
+bool matvec_batch_fp32(Handle *const *hs, int count, const void *const *x, void *const *y, const int64_t *ld,
+                       int64_t nrhs, int dtype, cudaStream_t s, cudaStream_t *workers, int nworkers, cudaEvent_t fork,
+                       cudaEvent_t *join);
 // wait budget and extra expected bytes of the FP32 kernels' staging (nnca_set_wait_test)
 void set_wait_test(int64_t wait_limit_clocks, unsigned extra_tx_bytes);
 void set_wait_test_tc(int64_t wait_limit_clocks, unsigned extra_tx_bytes);

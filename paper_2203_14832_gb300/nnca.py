@@ -44,7 +44,7 @@ class NncaError(RuntimeError):
 class _Config(C.Structure):
     _fields_ = [("d", C.c_int), ("leaf_size", C.c_int), ("eta2_num", C.c_int), ("eta2_den", C.c_int),
                 ("aca_tol", C.c_double), ("kernel", C.c_int), ("kparam", C.c_double * 4), ("symmetric", C.c_int),
-                ("m2l_form", C.c_int), ("reserved", C.c_int * 2)]
+                ("m2l_form", C.c_int), ("m2l_item_targets", C.c_int), ("reserved", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -110,11 +110,12 @@ class Config:
     kernel: int = K_INV_R
     kparam: tuple = (1.0, 0.0, 0.0, 0.0)
     m2l_form: int = M2L_AUTO
+    m2l_item_targets: int = 0
 
     def c(self) -> _Config:
         k = (C.c_double * 4)(*[float(v) for v in (list(self.kparam) + [0.0] * 4)[:4]])
         return _Config(self.d, self.leaf_size, self.eta2_num, self.eta2_den, float(self.aca_tol), self.kernel, k, 1,
-                       self.m2l_form, (C.c_int * 2)(0, 0))
+                       self.m2l_form, self.m2l_item_targets, 0)
 
 
 def _check(status: int, handle=None):

@@ -69,6 +69,38 @@ def test_batch_equals_single_products(gpu, orc):
 
 
 @pytest.mark.gpu
+def test_cross_problem_batch(gpu):
+    """Nine right-hand sides (two passes of four and one of one): the passes of four run
+    synchronised across the problems, the M2L of each pass as one launch per kernel family
+    over the cross-problem item list (1/r and Gaussian problems). Bit for bit the single
+    products, through a captured graph too, with the M2L tile tuned differently per problem."""
+    import torch
+    from paper_2203_14832_gb300 import batch
+    probs = small_batch(gpu, count=6, nrhs=9)
+    tiled = []
+    for k, (w, P, cfg, x) in enumerate(probs):
+        c = gpu.Config(d=3, leaf_size=32, aca_tol=w.aca_tol, kernel=w.kernel, kparam=w.kparam,
+                       m2l_item_targets=(0, 64, 128)[k % 3])
+        tiled.append((w, P, c, x))
+    b = batch.Batch([batch.Problem(P, cfg, x) for (_, P, cfg, x) in tiled], precision=gpu.PREC_FP32)
+    ys = [y.clone() for y in b.matvec()]
+    torch.cuda.synchronize()
+    for (w, P, cfg, x), h, y in zip(tiled, b.handles, ys):
+        assert torch.equal(h.matvec(x, gpu.PREC_FP32), y)
+        y64 = h.matvec(x, gpu.PREC_FP64)
+        assert float(torch.linalg.norm(y - y64) / torch.linalg.norm(y64)) < 1e-6
+        assert h.stats()["device_status"] & (2 | 16) == 0
+    g = b.capture()
+    for y in b.y:
+        y.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for y, r in zip(b.y, ys):
+        assert torch.equal(y, r)
+    b.close()
+
+
+@pytest.mark.gpu
 def test_batch_graph_replay(gpu):
     import torch
     from paper_2203_14832_gb300 import batch
@@ -97,9 +129,12 @@ def test_leaf_size_tuner(gpu):
     import torch
     from paper_2203_14832_gb300 import batch
     w, P, cfg, x = small_batch(gpu, count=1)[0]
-    h, times = batch.tune_leaf_size(P, cfg, x, candidates=(16, 32, 64), reps=2)
-    assert set(times) == {16, 32, 64} and all(t > 0 for t in times.values())
-    assert h.cfg.leaf_size == min(times, key=times.get)
+    h, times = batch.tune_leaf_size(P, cfg, x, candidates=(16, 32, 64), reps=2, tiles=(0, 64))
+    first = {nu: times[f"{nu}/0"] for nu in (16, 32, 64)}
+    nu = min(first, key=first.get)
+    assert set(times) == {"16/0", "32/0", "64/0", f"{nu}/64"} and all(t > 0 for t in times.values())
+    assert h.cfg.leaf_size == nu
+    assert h.cfg.m2l_item_targets == (64 if times[f"{nu}/64"] < times[f"{nu}/0"] else 0)
     y = h.matvec(x, gpu.PREC_FP64)
     h2 = gpu.H2(P, gpu.Config(d=3, leaf_size=64, aca_tol=w.aca_tol, kernel=w.kernel, kparam=w.kparam))
     y2 = h2.matvec(x, gpu.PREC_FP64)
