@@ -279,14 +279,26 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                 }
             }
             // let the copies of the last stages land (the latest phase of each
-            // stage's barrier), then mark the end of the block's work, also after a
-            // failure, so that the consumers stop
+            // stage's barrier), then mark the end of the block's work. The end
+            // marker arrives on a stage barrier only when that barrier's earlier
+            // phases all completed: after a failure a phase may still wait for
+            // bytes, and one more arrival would exceed its count; the consumers
+            // then stop on their own bounded waits instead.
+            bool clean = ok;
             for (unsigned j = cnt > (unsigned)TC_STAGES ? cnt - TC_STAGES : 0u; j < cnt; ++j)
-                if (!mbar_wait(&S.full[j % TC_STAGES], (j / TC_STAGES) & 1)) tc_fail(S, status);
+                if (!mbar_wait(&S.full[j % TC_STAGES], (j / TC_STAGES) & 1)) {
+                    tc_fail(S, status);
+                    clean = false;
+                }
             const int s = cnt % TC_STAGES;
-            if (cnt >= TC_STAGES && !mbar_wait(&S.freeb[s], (cnt / TC_STAGES - 1) & 1)) tc_fail(S, status);
-            S.st[s].flags = TC_END;
-            mbar_arrive(&S.full[s]);
+            if (cnt >= TC_STAGES && !mbar_wait(&S.freeb[s], (cnt / TC_STAGES - 1) & 1)) {
+                tc_fail(S, status);
+                clean = false;
+            }
+            if (clean && !*(volatile int *)&S.abort) {
+                S.st[s].flags = TC_END;
+                mbar_arrive(&S.full[s]);
+            }
         }
         __syncwarp();
     } else if (warp == 5) {

@@ -26,15 +26,20 @@ def test_bounded_waits_run_out_and_report(gpu):
     x = torch.as_tensor(w.make_vector(), device="cuda")
     X4 = torch.as_tensor(W.vector_normal(w.n, 3, nrhs=4), device="cuda")
     h = gpu.H2(P, cfg)
+    X16 = torch.as_tensor(W.vector_normal(w.n, 4, nrhs=16), device="cuda")
     ref1 = h.matvec(x, gpu.PREC_FP32).cpu().numpy()
     ref4 = h.matvec(X4, gpu.PREC_FP32).cpu().numpy()
+    ref16 = h.matvec(X16, gpu.PREC_TF32X3).cpu().numpy()
     assert h.stats()["device_status"] & (2 | DEV_WAIT_TIMEOUT) == 0
     gpu.nnca_set_wait_test(20000, 16)
     try:
-        # one right-hand side (symmetric M2L, grouped near field) and a pass of four
+        # one right-hand side (symmetric M2L, grouped near field), a pass of four
         # (M2L and near field of four right-hand sides): every wait runs out
         h.matvec(x, gpu.PREC_FP32)
         h.matvec(X4, gpu.PREC_FP32)
+        # the tensor-core M2L: its staging, evaluation and MMA roles all give up,
+        # the block waits for its copies and MMAs and frees its tensor memory
+        h.matvec(X16, gpu.PREC_TF32X3)
         torch.cuda.synchronize()
         assert h.stats()["device_status"] & DEV_WAIT_TIMEOUT
         # the synchronising host-buffer product reports the failed check
@@ -47,5 +52,6 @@ def test_bounded_waits_run_out_and_report(gpu):
     g = gpu.H2(P, cfg)
     assert np.array_equal(g.matvec(x, gpu.PREC_FP32).cpu().numpy(), ref1)
     assert np.array_equal(g.matvec(X4, gpu.PREC_FP32).cpu().numpy(), ref4)
+    assert np.array_equal(g.matvec(X16, gpu.PREC_TF32X3).cpu().numpy(), ref16)
     assert g.stats()["device_status"] & (2 | DEV_WAIT_TIMEOUT) == 0
     g.close()
