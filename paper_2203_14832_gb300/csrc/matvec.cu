@@ -298,6 +298,93 @@ __global__ void __launch_bounds__(32 * MV_WARPS) k_m2l_f64(KParams kp, int d, co
     }
 }
 
+// FP64 M2L of one right-hand side in the symmetric form: f(|p - q|) = f(|q - p|)
+// and Y in IL(X) exactly when X in IL(Y), so the warp of cell X evaluates only
+// the entries Y > X of its list, each value feeding the row sum of its target
+// a in X and the column sum of its source b in Y. The column sums of entry
+// (X, Y) go to slots slot[e] .. + r_Y (accumulated over X's chunks of 32
+// targets in order); k_m2l_f64_gather then adds, for every cell, the slots of
+// its entries Y < X in list order. Every order is fixed.
+template <int KIND>
+__global__ void __launch_bounds__(32 * MV_WARPS) k_m2l_f64_sym(KParams kp, int d, const int32_t *tgt, int64_t ntgt,
+                                                              const int32_t *il_off, const int32_t *il_idx,
+                                                              const int64_t *slot_of, const int32_t *piv_off,
+                                                              const double *pv, int64_t npiv, const double *w,
+                                                              double *u, double *slots) {
+    __shared__ double sx[MV_WARPS][4][32];
+    __shared__ double sw[MV_WARPS][32];
+    __shared__ double cs[MV_WARPS][32][33];   // column values of a chunk: [source][target lane], padded
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int64_t warp = blockIdx.x * (int64_t)MV_WARPS + wl;
+    const int64_t nw = (int64_t)gridDim.x * MV_WARPS;
+    for (int64_t t = warp; t < ntgt; t += nw) {
+        const int64_t X = tgt[t];
+        const int64_t p0 = piv_off[X], rX = piv_off[X + 1] - p0;
+        for (int64_t a0 = 0; a0 < rX; a0 += 32) {
+            const int64_t a = a0 + lane;
+            const bool act = a < rX;
+            double xa[4] = {0, 0, 0, 0};
+            if (act)
+                for (int k = 0; k < d; ++k) xa[k] = pv[(int64_t)k * npiv + p0 + a];
+            const double wa = act ? w[p0 + a] : 0.0;
+            double acc = 0.0;
+            for (int32_t e = il_off[X]; e < il_off[X + 1]; ++e) {
+                const int64_t Y = il_idx[e];
+                if (Y <= X) continue;
+                double *col = slots + slot_of[e];
+                const int64_t q0 = piv_off[Y], rY = piv_off[Y + 1] - q0;
+                for (int64_t b0 = 0; b0 < rY; b0 += 32) {
+                    const int64_t nb = min((int64_t)32, rY - b0);
+                    __syncwarp();
+                    if (lane < nb) {
+                        for (int k = 0; k < d; ++k) sx[wl][k][lane] = pv[(int64_t)k * npiv + q0 + b0 + lane];
+                        sw[wl][lane] = w[q0 + b0 + lane];
+                    }
+                    __syncwarp();
+                    for (int j = 0; j < nb; ++j) {
+                        double r2 = 0.0;
+                        for (int k = 0; k < d; ++k) {
+                            const double t2 = sx[wl][k][j] - xa[k];
+                            r2 = fma(t2, t2, r2);
+                        }
+                        const double f = act ? KF<KIND>::f64(kp, r2) : 0.0;
+                        acc = fma(f, sw[wl][j], acc);
+                        cs[wl][j][lane] = f * wa;
+                    }
+                    __syncwarp();
+                    // lane j sums column j over the targets, in lane order
+                    if (lane < nb) {
+                        double c = 0.0;
+                        for (int l = 0; l < 32; ++l) c += cs[wl][lane][l];
+                        col[b0 + lane] = a0 == 0 ? kp.s * c : col[b0 + lane] + kp.s * c;
+                    }
+                }
+            }
+            if (act) u[p0 + a] = kp.s * acc;
+        }
+    }
+}
+
+// u(X) += the column slots of X's entries Y < X, in list order
+__global__ void __launch_bounds__(32 * MV_WARPS) k_m2l_f64_gather(const int32_t *tgt, int64_t ntgt,
+                                                                 const int32_t *il_off, const int32_t *il_idx,
+                                                                 const int64_t *slot_of, const int32_t *piv_off,
+                                                                 const double *slots, double *u) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t = warp; t < ntgt; t += nw) {
+        const int64_t X = tgt[t];
+        const int64_t p0 = piv_off[X], rX = piv_off[X + 1] - p0;
+        for (int64_t a = lane; a < rX; a += 32) {
+            double v = u[p0 + a];
+            for (int32_t e = il_off[X]; e < il_off[X + 1]; ++e)
+                if (il_idx[e] < X) v += slots[slot_of[e] + a];
+            u[p0 + a] = v;
+        }
+    }
+}
+
 // ---- FP32 source streaming -----------------------------------------------------
 // A warp streams the sources of its source cells through a 64-entry ring in
 // shared memory and evaluates them in full chunks of 32. Sources are stored in
@@ -2212,6 +2299,42 @@ void launch_near_rhs(Handle *h, const double *op, const double *u, const double 
     ++h->launches;
 }
 
+// The slot tables of the symmetric FP64 M2L (built on the first FP64 product of
+// one right-hand side): per interaction-list entry e = (X, Y) with Y > X its
+// column slots' first index, and for an entry with Y < X the first slot of its
+// partner (Y, X); the slots themselves (one double per column of every entry
+// Y > X).
+void ensure_f64_sym(Handle *h) {
+    if (h->f64_slot_of || h->n_il == 0) return;
+    const int64_t nc = h->ncell, nil = h->n_il;
+    std::vector<int32_t> off(nc + 1), idx(nil);
+    NNCA_CUDA(cudaMemcpy(off.data(), h->il_off, (nc + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    NNCA_CUDA(cudaMemcpy(idx.data(), h->il_idx, nil * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    std::vector<int64_t> slot(nil, -1);
+    int64_t total = 0;
+    for (int64_t X = 0; X < nc; ++X)
+        for (int32_t e = off[X]; e < off[X + 1]; ++e) {
+            const int32_t Y = idx[e];
+            if (Y > X) {
+                slot[e] = total;
+                total += h->h_piv_off[Y + 1] - h->h_piv_off[Y];
+            }
+        }
+    for (int64_t X = 0; X < nc; ++X)
+        for (int32_t e = off[X]; e < off[X + 1]; ++e) {
+            const int32_t Y = idx[e];
+            if (Y >= X) continue;
+            // the partner entry (Y, X) in Y's list (lists are in ascending cell order)
+            const int32_t *b = idx.data() + off[Y], *eend = idx.data() + off[Y + 1];
+            const int32_t *f = std::lower_bound(b, eend, (int32_t)X);
+            NNCA_REQUIRE(f != eend && *f == X, NNCA_ERR_INTERNAL, "interaction lists are not symmetric");
+            slot[e] = slot[off[Y] + (f - b)];
+        }
+    h->f64_slot_of = dalloc<int64_t>(h, nil);
+    NNCA_CUDA(cudaMemcpy(h->f64_slot_of, slot.data(), nil * sizeof(int64_t), cudaMemcpyHostToDevice));
+    h->f64_slots = dalloc<double>(h, std::max<int64_t>(total, 1));
+}
+
 void ensure_workspace(Handle *h, int64_t nrhs) {
     if (h->ws && h->ws_nrhs >= nrhs) return;
     if (h->ws) {
@@ -2353,6 +2476,16 @@ void run_chunk(Handle *h, const void *x, void *y, int64_t ld, int64_t r0) {
                 launch_m2l_f32<KIND>(h, u);
             } else if (FP32 && NR == M2L_RHS) {
                 launch_m2l_f32_rhs<KIND>(h, u);
+            } else if (NR == 1 && (h->f64_slot_of || !h->no_alloc)) {
+                // FP64, one right-hand side: each admissible pair of cells evaluated once
+                ensure_f64_sym(h);
+                k_m2l_f64_sym<KIND><<<g, 32 * MV_WARPS, 0, s>>>(h->kp, h->d, h->m2l_tgt, h->n_m2l_tgt, h->il_off,
+                                                               h->il_idx, h->f64_slot_of, h->piv_off, h->pv64, npiv,
+                                                               w, u, h->f64_slots);
+                NNCA_LAUNCH_CHECK();
+                k_m2l_f64_gather<<<g, 32 * MV_WARPS, 0, s>>>(h->m2l_tgt, h->n_m2l_tgt, h->il_off, h->il_idx,
+                                                             h->f64_slot_of, h->piv_off, h->f64_slots, u);
+                ++h->launches;
             } else {
                 k_m2l_f64<KIND, NR><<<g, 32 * MV_WARPS, 0, s>>>(h->kp, h->d, h->m2l_tgt, h->n_m2l_tgt, h->il_off,
                                                                 h->il_idx, h->piv_off, h->pv64, npiv, w, u);

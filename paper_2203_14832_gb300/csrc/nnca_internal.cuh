@@ -355,6 +355,9 @@ struct Handle {
     // tensor-core M2L of many right-hand sides: items (parent, first target |
     // targets << 16, first record, records) of at most 64 targets over the full
     // plan (m2l_plan), heaviest first
+    bool no_alloc = false;            // inside nnca_matvec_noalloc: no path may allocate
+    int64_t *f64_slot_of = nullptr;   // symmetric FP64 M2L: first column slot of each IL entry (or its partner's)
+    double *f64_slots = nullptr;
     int4 *tc_items = nullptr;
     int n_tc_items = 0;
     int2 *leaf_items[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};

@@ -95,6 +95,7 @@ extern "C" nnca_status nnca_matvec_noalloc(nnca_handle hh, const void *x, void *
     h->ws = scratch;
     h->ws_bytes = kScratchBytes;
     h->ws_nrhs = 1;
+    h->no_alloc = true;   // paths that would allocate their tables take their allocation-free form
     st = NNCA_OK;
     try {
         h->stream = (cudaStream_t)stream;
@@ -110,5 +111,6 @@ extern "C" nnca_status nnca_matvec_noalloc(nnca_handle hh, const void *x, void *
     h->ws = saved_ws;
     h->ws_bytes = saved_bytes;
     h->ws_nrhs = saved_nrhs;
+    h->no_alloc = false;
     return st;
 }
