@@ -21,10 +21,9 @@
  *     f2 <- f2 + 2*cross, f2 <- f2 + |u|^2*|v|^2.
  *  6. Stopping rule (Eq. 4): stop when |u|_2 |v|_2 <= eps ||A^(k+1)||_F,
  *     evaluated as sqrt(|u|^2) * sqrt(|v|^2) <= eps * sqrt(f2). The cross that
- *     meets the rule is NOT kept: it is negligible at tolerance eps, and
- *     keeping it would put an (up to) round-off-sized Schur complement into the
- *     pivot submatrix A_{tau sigma} that the bases of Sec. 2.3.1 invert (for a
- *     block of exact rank r it would keep a pure round-off (r+1)-th pivot).
+ *     meets the rule is NOT kept: it is negligible at tolerance eps, so the
+ *     rank is the smallest that meets the rule, and a block of exact rank r
+ *     gets exactly r pivots (keeping it would add a pure round-off (r+1)-th).
  *  7. Otherwise the cross is kept (pivots (i, j*)), and the iteration stops
  *     when k = min(m, n) or no unused row is left; the next row is the argmax
  *     over unused rows of |u(i')|, ties to the smallest i'.
