@@ -97,6 +97,7 @@ nnca_status fail(Handle *h, nnca_status s, const std::string &msg) {
 void free_all(Handle *h) {
     cudaDeviceSynchronize();
     cudaGetLastError();
+    release_cross_plans(h->uid);
     for (cudaEvent_t e : h->prof_events) cudaEventDestroy(e);
     for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
     h->prof_events.clear();

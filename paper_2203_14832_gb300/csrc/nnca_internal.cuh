@@ -398,6 +398,8 @@ void matvec(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int dty
 bool matvec_batch_fp32(Handle *const *hs, int count, const void *const *x, void *const *y, const int64_t *ld,
                        int64_t nrhs, int dtype, cudaStream_t s, cudaStream_t *workers, int nworkers, cudaEvent_t fork,
                        cudaEvent_t *join);
+// frees the cross-problem item lists of every handle set that contains handle uid
+void release_cross_plans(uint64_t uid);
 // wait budget and extra expected bytes of the FP32 kernels' staging (nnca_set_wait_test)
 void set_wait_test(int64_t wait_limit_clocks, unsigned extra_tx_bytes);
 void set_wait_test_tc(int64_t wait_limit_clocks, unsigned extra_tx_bytes);
