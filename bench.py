@@ -376,8 +376,7 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     peak_gpair = MUFU_PER_CLK_SM * sms * sm_max * 1e6 / 1e9
     tc = args.precision != "fp32"
-    passes = pass_rooflines(h, st, pass_ms, sms, sm_max, peaks, min(nrhs, 64) if tc else (nrhs if nrhs < 4 else 4),
-                            args.precision)
+    passes = pass_rooflines(h, st, pass_ms, sms, sm_max, peaks, nrhs, args.precision)
     # kernel evaluations of the pass: each pivot pair once in the symmetric form
     # (a value serves the row and the column sum), else every ordered pair
     evals = st.get("m2l_evals") or st["m2l_pairs"]
@@ -393,6 +392,25 @@ def run_ours(args):
             traffic, traffic_note = tj.get("bytes_per_launch"), tj.get("note")
         except Exception:
             traffic = None
+
+    roofline = {"bound": "alu", "kernel": m2l_kernel, "achieved": achieved, "peak": peak_gpair,
+                "unit": "G kernel evaluations/s", "frac": achieved / peak_gpair, "traffic": traffic,
+                "peak_note": f"one MUFU rsqrt per evaluation: {MUFU_PER_CLK_SM}/clk/SM x {sms} SMs x "
+                             f"{sm_max:.0f} MHz",
+                "pairs_served_per_s_frac": st["m2l_pairs"] / (m2l_ms / 1e3) / 1e9 / peak_gpair,
+                "pairs_note": "symmetric form: each evaluation feeds two ordered pivot pairs (a row and "
+                              "a column sum); this fraction counts those pairs against the same peak",
+                "traffic_note": ("DRAM bytes read + written by one M2L launch: " + traffic_note) if traffic_note
+                else "no full-size ncu DRAM figure for this kernel and workload"}
+    if tc or nrhs > 1:
+        # several right-hand sides: the M2L pass's own entry (tensor-core flops, or
+        # MUFU evaluations of the four-RHS kernel summed over the product's passes)
+        p0 = passes[0]
+        scale = 1e12 if p0["unit"] == "flops" else 1e9
+        roofline = {"bound": p0["bound"], "kernel": p0["kernels"], "achieved": p0["achieved"] / scale,
+                    "peak": p0["peak"] / scale, "unit": "TFLOP/s" if p0["unit"] == "flops" else "G kernel evaluations/s",
+                    "frac": p0["frac"], "traffic": None, "peak_note": p0["note"],
+                    "traffic_note": "no full-size ncu DRAM figure for this kernel and workload"}
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -415,15 +433,7 @@ def run_ours(args):
         "work": {"m2l_pairs": st["m2l_pairs"], "m2l_evals": evals, "p2p_pairs": st["p2p_pairs"]},
         "pass_ms": {"perm": pass_ms[0], "p2m_m2m": pass_ms[1], "m2l": pass_ms[2], "l2l": pass_ms[3],
                     "l2p_p2p": pass_ms[4], "total": pass_ms[5]},
-        "roofline": {"bound": "alu", "kernel": m2l_kernel, "achieved": achieved, "peak": peak_gpair,
-                     "unit": "G kernel evaluations/s", "frac": achieved / peak_gpair, "traffic": traffic,
-                     "peak_note": f"one MUFU rsqrt per evaluation: {MUFU_PER_CLK_SM}/clk/SM x {sms} SMs x "
-                                  f"{sm_max:.0f} MHz",
-                     "pairs_served_per_s_frac": st["m2l_pairs"] / (m2l_ms / 1e3) / 1e9 / peak_gpair,
-                     "pairs_note": "symmetric form: each evaluation feeds two ordered pivot pairs (a row and "
-                                   "a column sum); this fraction counts those pairs against the same peak",
-                     "traffic_note": ("DRAM bytes read + written by one M2L launch: " + traffic_note) if traffic_note
-                     else "no full-size ncu DRAM figure for this kernel and workload"},
+        "roofline": roofline,
         "roofline_passes": passes,
         "dominant_pass": max((p for p in passes if p.get("ms")), key=lambda p: p["ms"])["pass"],
         "e2e": {"value": e2e_value, "unit": "points/s", "h2d_bytes_per_step": N * nrhs * 8,
@@ -440,9 +450,10 @@ def run_ours(args):
         sys.exit(3)
 
 
-def pass_rooflines(h, st, pass_ms, sms, sm_mhz, peaks, nr, precision="fp32"):
-    """Achieved fraction of its roofline for every pass of one FP32 product (pass
-    times from CUDA events on the launching stream; nr right-hand sides per pass).
+def pass_rooflines(h, st, pass_ms, sms, sm_mhz, peaks, nrhs, precision="fp32"):
+    """Achieved fraction of its roofline for every pass of one product of nrhs
+    right-hand sides (pass times from CUDA events on the launching stream, summed
+    over the product's passes; the work below is summed the same way).
 
     Algorithmic work per pass (counted exactly from the built representation):
       M2L     kernel evaluations (m2l_evals), one MUFU rsqrt each
@@ -468,33 +479,45 @@ def pass_rooflines(h, st, pass_ms, sms, sm_mhz, peaks, nr, precision="fp32"):
         return {"pass": name, "kernels": kernels, "bound": bound, "work": work, "unit": unit, "ms": ms,
                 "achieved": ach, "peak": peak, "frac": ach / peak if peak else None, "note": note}
 
-    # one RHS: the symmetric form evaluates each pivot pair once; passes of four: every
-    # ordered pair once for the four
-    evals = (st.get("m2l_evals") or st["m2l_pairs"]) if nr == 1 else st["m2l_pairs"]
-    grp = 8 if precision != "fp32" else 4   # right-hand sides per operator pass
+    # How the product groups its right-hand sides. FP32 form: passes of four (every
+    # ordered pivot pair evaluated once for the four; near field and operators once
+    # per pass), the rest one at a time (symmetric M2L: each pivot pair once).
+    # Tensor-core forms: M2L passes of up to 64, operators in groups of eight (then
+    # four, then one), near field in groups of four (then one).
+    sym_evals = st.get("m2l_evals") or st["m2l_pairs"]
+    if precision == "fp32":
+        quads, singles = nrhs // 4, nrhs % 4
+        m2l_work = st["m2l_pairs"] * quads + sym_evals * singles
+        near_groups = quads + singles
+        op_groups = quads + singles
+    else:
+        near_groups = nrhs // 4 + nrhs % 4
+        op_groups = nrhs // 8 + (nrhs % 8) // 4 + nrhs % 4
     if precision != "fp32":
         # tensor-core M2L: useful flops of the contraction (2 per pivot pair and
         # right-hand side, times the products per pair), against the tf32 dense
         # peak = measured bf16 peak x nominal tf32/bf16 ratio (1.1 / 2.25)
         prods = 3 if precision == "tf32x3" else 1
         bf16 = float(peaks.get("bf16_tflops", 1900.0)) * 1e12
-        m2l = ent("m2l", "k_m2l_tc (+ pack, unpack)", "tensor", 2.0 * prods * st["m2l_pairs"] * nr, "flops", pass_ms[2],
-                  bf16 * 1.1 / 2.25, f"{prods} tf32 products per pivot pair and right-hand side, {nr} right-hand "
-                  "sides per pass; peak: measured bf16 x 1.1/2.25" + ("" if "bf16_tflops" in peaks else " (fallback)"))
+        m2l = ent("m2l", "k_m2l_tc (+ pack, unpack)", "tensor", 2.0 * prods * st["m2l_pairs"] * nrhs, "flops",
+                  pass_ms[2], bf16 * 1.1 / 2.25, f"{prods} tf32 products per pivot pair and right-hand side, up to "
+                  "64 right-hand sides per pass; peak: measured bf16 x 1.1/2.25"
+                  + ("" if "bf16_tflops" in peaks else " (fallback)"))
         m2l["mufu_frac"] = st["m2l_pairs"] / (pass_ms[2] / 1e3) / (MUFU_PER_CLK_SM * sms * clk) if pass_ms[2] else None
     else:
-        m2l = ent("m2l", "k_m2l_sym + k_m2l_cols" if nr == 1 else "k_m2l_group_rhs", "alu", evals, "kernel evaluations",
-                  pass_ms[2], MUFU_PER_CLK_SM * sms * clk, "one MUFU rsqrt (or ex2) per kernel evaluation")
+        m2l = ent("m2l", "k_m2l_sym + k_m2l_cols" if nrhs == 1 else "k_m2l_group_rhs", "alu", m2l_work,
+                  "kernel evaluations", pass_ms[2], MUFU_PER_CLK_SM * sms * clk,
+                  "one MUFU rsqrt (or ex2) per kernel evaluation")
     out = [
         m2l,
-        ent("l2p_p2p", "k_near_group" if nr == 1 else "k_near_rhs", "alu", st["p2p_pairs"] * max(1, nr // 4),
+        ent("l2p_p2p", "k_near_group" if nrhs == 1 else "k_near_rhs", "alu", st["p2p_pairs"] * near_groups,
             "point pairs (evaluations)", pass_ms[4], FP32_PER_CLK_SM / NEAR_OPS_PER_PAIR * sms * clk,
             f"FP32 pipe at {NEAR_OPS_PER_PAIR} lane-ops per pair, one evaluation per pair and group of up to 4 "
             "right-hand sides; includes the FP64 L2P of the same kernel"),
-        ent("p2m_m2m", "k_upward", "hbm", 8 * (op_all * max(1, nr // grp) + nr * (n + npiv)), "bytes", pass_ms[1], hbm,
-            "FP64 operators of every cell + x in tree order + w; " + hbm_note),
-        ent("l2l", "k_l2l", "hbm", 8 * (op_nonleaf * max(1, nr // grp) + 2 * nr * npiv), "bytes", pass_ms[3], hbm,
-            "FP64 translations of the non-leaf cells + u read and written; " + hbm_note),
+        ent("p2m_m2m", "k_upward", "hbm", 8 * (op_all * op_groups + nrhs * (n + npiv)), "bytes", pass_ms[1], hbm,
+            "FP64 operators of every cell (once per group of right-hand sides) + x in tree order + w; " + hbm_note),
+        ent("l2l", "k_l2l", "hbm", 8 * (op_nonleaf * op_groups + 2 * nrhs * npiv), "bytes", pass_ms[3], hbm,
+            "FP64 translations of the non-leaf cells (once per group) + u read and written; " + hbm_note),
     ]
     af = os.path.join(ROOT, "profiles", "aca_invr3d_131k.json")
     if os.path.exists(af):
