@@ -1589,6 +1589,7 @@ void build_finish(Handle *h) {
             h->near_items4 = dalloc<int4>(h, v4.size());
             if (!v4.empty())
                 NNCA_CUDA(cudaMemcpy(h->near_items4, v4.data(), v4.size() * sizeof(int4), cudaMemcpyHostToDevice));
+            h->near_pairs = npairs;
             h->pw4 = dalloc<float4>(h, 2 * (size_t)npairs);
             NNCA_CUDA(cudaMemsetAsync(h->pw4, 0, 2 * (size_t)npairs * sizeof(float4), s));
         }

@@ -1283,14 +1283,16 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_near_group(KParams kp, cons
 // each kernel value feeds the four right-hand sides' accumulators, whose source
 // weights come from pw4 (two float4 per point pair, L2-resident) beside the
 // staged coordinates. L2P of the four and the diagonal term follow in the warp.
-struct NearTarget4 {
+template <int NR> struct NearTarget4 {
     bool act = false;
     int i = 0;
     f2 xh = F2Z, yh = F2Z, zh = F2Z, xl = F2Z, yl = F2Z, zl = F2Z;
-    float sum[M2L_RHS] = {0.f, 0.f, 0.f, 0.f}, comp[M2L_RHS] = {0.f, 0.f, 0.f, 0.f};
+    float sum[NR] = {}, comp[NR] = {};
 };
 
-__device__ __forceinline__ void near_target4(NearTarget4 &T, bool act, int i, const float4 *xh4, const float4 *xl4) {
+template <int NR>
+__device__ __forceinline__ void near_target4(NearTarget4<NR> &T, bool act, int i, const float4 *xh4,
+                                             const float4 *xl4) {
     T.act = act;
     T.i = i;
     if (!act) return;
@@ -1304,33 +1306,35 @@ __device__ __forceinline__ void near_target4(NearTarget4 &T, bool act, int i, co
 }
 
 // fold a cell's partial sums (acc[k][r]) into the compensated totals
-__device__ __forceinline__ void near4_fold(NearTarget4 (&T)[2], f2 (&acc)[2][M2L_RHS]) {
+template <int NR>
+__device__ __forceinline__ void near4_fold(NearTarget4<NR> (&T)[2], f2 (&acc)[2][NR]) {
 #pragma unroll
     for (int k = 0; k < 2; ++k)
 #pragma unroll
-        for (int r = 0; r < M2L_RHS; ++r) {
+        for (int r = 0; r < NR; ++r) {
             const float2 p = f2_unpack(acc[k][r]);
             two_sum_add(T[k].sum[r], T[k].comp[r], p.x + p.y);
         }
 }
 
-// an adjacent cell (hi/lo pairs at P[4 q], weights of pair q at W[2 q]): this
-// lane's group takes pairs g, g + G, ...
-template <int KIND, bool SAFE>
+// an adjacent cell (hi/lo pairs at P[4 q], weights of pair q at W[NR / 2 q]):
+// this lane's group takes pairs g, g + G, ...
+template <int KIND, bool SAFE, int NR>
 __device__ __forceinline__ void near4_cell(const KParams &kp, const float4 *P, const float4 *W, int np, int g, int G,
-                                           NearTarget4 (&T)[2]) {
-    f2 acc[2][M2L_RHS];
+                                           NearTarget4<NR> (&T)[2]) {
+    f2 acc[2][NR];
 #pragma unroll
     for (int k = 0; k < 2; ++k)
 #pragma unroll
-        for (int r = 0; r < M2L_RHS; ++r) acc[k][r] = F2Z;
+        for (int r = 0; r < NR; ++r) acc[k][r] = F2Z;
     for (int q = g; q < np; q += G) {
         const f2x2 A = ld2(&P[4 * q]);
         const f2x2 B = ld2(&P[4 * q + 1]);
         const f2x2 C = ld2(&P[4 * q + 2]);
         const f2x2 D = ld2(&P[4 * q + 3]);
-        const f2x2 w01 = ldg2(&W[2 * q]);
-        const f2x2 w23 = ldg2(&W[2 * q + 1]);
+        f2x2 wv[NR / 2];
+#pragma unroll
+        for (int r2 = 0; r2 < NR / 2; ++r2) wv[r2] = ldg2(&W[(NR / 2) * q + r2]);
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const f2 dx = f2_add(f2_sub(A.x, T[k].xh), f2_sub(C.x, T[k].xl));
@@ -1340,20 +1344,21 @@ __device__ __forceinline__ void near4_cell(const KParams &kp, const float4 *P, c
             r2 = f2_fma(dy, dy, r2);
             r2 = f2_fma(dz, dz, r2);
             const f2 f = KF2<KIND, SAFE>::eval(kp, r2);
-            acc[k][0] = f2_fma(f, w01.x, acc[k][0]);
-            acc[k][1] = f2_fma(f, w01.y, acc[k][1]);
-            acc[k][2] = f2_fma(f, w23.x, acc[k][2]);
-            acc[k][3] = f2_fma(f, w23.y, acc[k][3]);
+#pragma unroll
+            for (int r2 = 0; r2 < NR / 2; ++r2) {
+                acc[k][2 * r2] = f2_fma(f, wv[r2].x, acc[k][2 * r2]);
+                acc[k][2 * r2 + 1] = f2_fma(f, wv[r2].y, acc[k][2 * r2 + 1]);
+            }
         }
     }
     near4_fold(T, acc);
 }
 
 // a leaf at least one leaf away (pairs relative to its centre at P[2 q])
-template <int KIND>
+template <int KIND, int NR>
 __device__ __forceinline__ void near4_cell_far(const KParams &kp, const float4 *P, const float4 *W, int np, int g,
-                                               int G, float4 ch, float4 cl, NearTarget4 (&T)[2]) {
-    f2 tx[2], ty[2], tz[2], acc[2][M2L_RHS];
+                                               int G, float4 ch, float4 cl, NearTarget4<NR> (&T)[2]) {
+    f2 tx[2], ty[2], tz[2], acc[2][NR];
     {
         const f2 hx = f2_pack(ch.x, ch.x), hy = f2_pack(ch.y, ch.y), hz = f2_pack(ch.z, ch.z);
         const f2 lx = f2_pack(cl.x, cl.x), ly = f2_pack(cl.y, cl.y), lz = f2_pack(cl.z, cl.z);
@@ -1363,29 +1368,32 @@ __device__ __forceinline__ void near4_cell_far(const KParams &kp, const float4 *
             ty[k] = f2_add(f2_sub(T[k].yh, hy), f2_sub(T[k].yl, ly));
             tz[k] = f2_add(f2_sub(T[k].zh, hz), f2_sub(T[k].zl, lz));
 #pragma unroll
-            for (int r = 0; r < M2L_RHS; ++r) acc[k][r] = F2Z;
+            for (int r = 0; r < NR; ++r) acc[k][r] = F2Z;
         }
     }
     for (int q = g; q < np; q += G) {
         const f2x2 A = ld2(&P[2 * q]);
         const f2x2 B = ld2(&P[2 * q + 1]);
-        const f2x2 w01 = ldg2(&W[2 * q]);
-        const f2x2 w23 = ldg2(&W[2 * q + 1]);
+        f2x2 wv[NR / 2];
+#pragma unroll
+        for (int r2 = 0; r2 < NR / 2; ++r2) wv[r2] = ldg2(&W[(NR / 2) * q + r2]);
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const f2 f = near_group_f<KIND>(kp, A, B, tx[k], ty[k], tz[k]);
-            acc[k][0] = f2_fma(f, w01.x, acc[k][0]);
-            acc[k][1] = f2_fma(f, w01.y, acc[k][1]);
-            acc[k][2] = f2_fma(f, w23.x, acc[k][2]);
-            acc[k][3] = f2_fma(f, w23.y, acc[k][3]);
+#pragma unroll
+            for (int r2 = 0; r2 < NR / 2; ++r2) {
+                acc[k][2 * r2] = f2_fma(f, wv[r2].x, acc[k][2 * r2]);
+                acc[k][2 * r2 + 1] = f2_fma(f, wv[r2].y, acc[k][2 * r2 + 1]);
+            }
         }
     }
     near4_fold(T, acc);
 }
 
 // items: (leaf, first target | targets << 16 | groups << 24, first record, records);
-// u, xt64: M2L_RHS rows of npiv and N; y: M2L_RHS rows of ld
-template <int KIND, class TO>
+// u, xt64: NR rows of npiv and N; y: NR rows of ld; pw: NR / 2 float4 of weights
+// per point pair (k_near_weights4<NR>)
+template <int KIND, class TO, int NR>
 __global__ void __launch_bounds__(32 * NEAR_WARPS) k_near_rhs(KParams kp, const int4 *items, int nitems,
                                                              int *next_item, const int4 *plan, const int32_t *cbeg,
                                                              const int32_t *piv_off, const int64_t *op_off,
@@ -1418,7 +1426,7 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_near_rhs(KParams kp, const 
         const int g = lane / L, ti = lane - g * L;
         const bool live = g < G;
         const int i0 = cbeg[B] + f0;
-        NearTarget4 T[2];
+        NearTarget4<NR> T[2];
 #pragma unroll
         for (int k = 0; k < 2; ++k) near_target4(T[k], live && ti * 2 + k < c, i0 + ti * 2 + k, xh4, xl4);
         int kprod = item.z, kcons = item.z;
@@ -1450,11 +1458,11 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_near_rhs(KParams kp, const 
                 for (int e = 0; e < nrec; ++e) {
                     const int hw = W.hdr[b][e];
                     const float4 *P = &W.u[b][hw & 0x7ff];
-                    const float4 *Wt = pw4 + 2 * (int64_t)pq[wl][b][e];
+                    const float4 *Wt = pw4 + (NR / 2) * (int64_t)pq[wl][b][e];
                     const int np = (hw >> 11) & 0x7ff;
-                    if (!((hw >> 23) & 1)) near4_cell_far<KIND>(kp, P, Wt, np, g, G, W.ch[b][e], W.cl[b][e], T);
-                    else if ((hw >> 22) & 1) near4_cell<KIND, true>(kp, P, Wt, np, g, G, T);
-                    else near4_cell<KIND, false>(kp, P, Wt, np, g, G, T);
+                    if (!((hw >> 23) & 1)) near4_cell_far<KIND, NR>(kp, P, Wt, np, g, G, W.ch[b][e], W.cl[b][e], T);
+                    else if ((hw >> 22) & 1) near4_cell<KIND, true, NR>(kp, P, Wt, np, g, G, T);
+                    else near4_cell<KIND, false, NR>(kp, P, Wt, np, g, G, T);
                 }
             __syncwarp();
             ++R;
@@ -1466,7 +1474,7 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_near_rhs(KParams kp, const 
 #pragma unroll
             for (int k = 0; k < 2; ++k)
 #pragma unroll
-                for (int r = 0; r < M2L_RHS; ++r) {
+                for (int r = 0; r < NR; ++r) {
                     const float so = __shfl_sync(0xffffffffu, T[k].sum[r], srcl);
                     const float co = __shfl_sync(0xffffffffu, T[k].comp[r], srcl);
                     if (g == 0) {
@@ -1476,21 +1484,21 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k_near_rhs(KParams kp, const 
                 }
         }
         if (g == 0) {
-            // L2P of the four in FP64 (one pass over the row of U_B), then the diagonal
+            // L2P of the NR in FP64 (one pass over the row of U_B), then the diagonal
             const int rk = piv_off[B + 1] - piv_off[B];
             const int64_t ub = piv_off[B];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 if (!T[k].act) continue;
                 const double *Urow = op + op_off[B] + (int64_t)(T[k].i - cbeg[B]) * rk;
-                double far[M2L_RHS] = {0.0, 0.0, 0.0, 0.0};
+                double far[NR] = {};
                 for (int bb = 0; bb < rk; ++bb) {
                     const double ue = Urow[bb];
 #pragma unroll
-                    for (int r = 0; r < M2L_RHS; ++r) far[r] = fma(ue, u[r * npiv + ub + bb], far[r]);
+                    for (int r = 0; r < NR; ++r) far[r] = fma(ue, u[r * npiv + ub + bb], far[r]);
                 }
 #pragma unroll
-                for (int r = 0; r < M2L_RHS; ++r) {
+                for (int r = 0; r < NR; ++r) {
                     const double near = (double)T[k].sum[r] + (double)T[k].comp[r];
                     const double yv =
                         far[r] + kp.s * near + (kp.diag - kp.s * (double)k0) * xt64[r * N + T[k].i];
@@ -1508,7 +1516,9 @@ using nf::k_near_group;
 using nf::k_near_rhs;
 #undef F2Z
 
-// the four right-hand sides' FP32 weights of every leaf point into pw4
+// the NR right-hand sides' FP32 weights of every leaf point into pw: per point
+// pair q, NR / 2 float4 [w(2q, r) w(2q+1, r) w(2q, r+1) w(2q+1, r+1)], r even
+template <int NR>
 __global__ void k_near_weights4(int64_t N, const double *xt, float *pw4, const int32_t *leaf_of, const int32_t *cbeg,
                                 const int32_t *ppk_off) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
@@ -1516,7 +1526,7 @@ __global__ void k_near_weights4(int64_t N, const double *xt, float *pw4, const i
         const int64_t j = i - cbeg[B];
         const int64_t q = (int64_t)ppk_off[B] + (j >> 1);
 #pragma unroll
-        for (int r = 0; r < M2L_RHS; ++r) pw4[8 * q + (r >> 1) * 4 + (r & 1) * 2 + (j & 1)] = (float)xt[r * N + i];
+        for (int r = 0; r < NR; ++r) pw4[2 * NR * q + (r >> 1) * 4 + (r & 1) * 2 + (j & 1)] = (float)xt[r * N + i];
     }
 }
 
@@ -2356,20 +2366,27 @@ void launch_leaf_f32(Handle *h, const double *op, const double *u, const float *
     }
 }
 
-// the near field of M2L_RHS right-hand sides (u, xt64: M2L_RHS rows; y: rows of ld)
-template <int KIND, class TO>
-void launch_near_rhs(Handle *h, const double *op, const double *u, const double *xt64, TO *y, int64_t ld) {
+// the near field of NR right-hand sides (u, xt64: NR rows; y: rows of ld): their
+// weights into pw (NR / 2 float4 per point pair), then one pass over the leaves
+template <int KIND, class TO, int NR>
+void launch_near_rhs(Handle *h, const double *op, const double *u, const double *xt64, TO *y, int64_t ld, float4 *pw) {
+    NNCA_REQUIRE(pw != nullptr, NNCA_ERR_INTERNAL, "near-field weights of this group size not allocated");
+    const int64_t N = h->n;
+    k_near_weights4<NR><<<grid_for(N, 256), 256, 0, h->stream>>>(N, xt64, reinterpret_cast<float *>(pw), h->leaf_of,
+                                                                 h->cbeg, h->ppk_off);
+    NNCA_LAUNCH_CHECK();
+    ++h->launches;
     int dev = 0, nsm = 152, per_sm = 1;
     NNCA_CUDA(cudaGetDevice(&dev));
     NNCA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    NNCA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_near_rhs<KIND, TO>, 32 * NEAR_WARPS, 0));
+    NNCA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_near_rhs<KIND, TO, NR>, 32 * NEAR_WARPS, 0));
     const int n = h->n_near_items4;
     const int64_t warps = (int64_t)nsm * std::max(1, per_sm) * NEAR_WARPS;
     const unsigned g = (unsigned)((std::min<int64_t>(n, warps) + NEAR_WARPS - 1) / NEAR_WARPS);
     NNCA_CUDA(cudaMemsetAsync(h->near_next + 2, 0, sizeof(int), h->stream));
-    k_near_rhs<KIND, TO><<<g, 32 * NEAR_WARPS, 0, h->stream>>>(
+    k_near_rhs<KIND, TO, NR><<<g, 32 * NEAR_WARPS, 0, h->stream>>>(
         h->kp, h->near_items4, n, h->near_next + 2, h->near_plan, h->cbeg, h->piv_off, h->op_off, op, u, h->npiv,
-        h->xh4, h->xl4, h->chi4, h->clo4, h->ppk, h->ppl, h->pw4, xt64, h->n, h->perm, y, ld, h->dev_status);
+        h->xh4, h->xl4, h->chi4, h->clo4, h->ppk, h->ppl, pw, xt64, h->n, h->perm, y, ld, h->dev_status);
     NNCA_LAUNCH_CHECK();
     ++h->launches;
 }
@@ -2491,11 +2508,10 @@ void pass_near(Handle *h, const double *u, const double *xt, const float *xt32, 
         launch_leaf_f32<KIND, TO>(h, op, u, xt32, xt, yout);
     } else if (FP32 && NR == M2L_RHS && h->near_packed && h->n_near_items4) {
         // the near field of the four right-hand sides in one pass
-        k_near_weights4<<<grid_for(N, 256), 256, 0, s>>>(N, xt, reinterpret_cast<float *>(h->pw4), h->leaf_of, h->cbeg,
-                                                         h->ppk_off);
-        NNCA_LAUNCH_CHECK();
-        ++h->launches;
-        launch_near_rhs<KIND, TO>(h, op, u, xt, yout, ld);
+        launch_near_rhs<KIND, TO, M2L_RHS>(h, op, u, xt, yout, ld, h->pw4);
+    } else if (FP32 && NR == 2 * M2L_RHS && h->near_packed && h->n_near_items4 && h->pw8) {
+        // eight in one pass (tensor-core forms): each kernel value serves eight
+        launch_near_rhs<KIND, TO, 2 * M2L_RHS>(h, op, u, xt, yout, ld, h->pw8);
     } else if (FP32) {
         // the near field one right-hand side at a time
         for (int r = 0; r < NR; ++r) {
@@ -2642,7 +2658,10 @@ void run_tc(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int mod
             }
         prof_mark(h, 4);
         for (int r = 0; r < nr;) {
-            if (nr - r >= M2L_RHS) {
+            if (nr - r >= 2 * M2L_RHS && h->pw8) {
+                pass_near<true, 2 * M2L_RHS, KIND, TO>(h, u + r * npiv, xt + r * N, xt32 + r * N, yout + r * ld, ld);
+                r += 2 * M2L_RHS;
+            } else if (nr - r >= M2L_RHS) {
                 pass_near<true, M2L_RHS, KIND, TO>(h, u + r * npiv, xt + r * N, xt32 + r * N, yout + r * ld, ld);
                 r += M2L_RHS;
             } else {
@@ -2673,6 +2692,10 @@ void ensure_tc_workspace(Handle *h) {
     h->tc_ws_bytes = bytes;
     // the packed weights' padding must read as zero: clear once
     NNCA_CUDA(cudaMemsetAsync(h->tc_ws, 0, bytes, h->stream));
+    if (!h->pw8 && h->near_packed && h->n_near_items4) {
+        h->pw8 = dalloc<float4>(h, 4 * (size_t)h->near_pairs);
+        NNCA_CUDA(cudaMemsetAsync(h->pw8, 0, 4 * (size_t)h->near_pairs * sizeof(float4), h->stream));
+    }
 }
 
 template <bool FP32, int KIND, class TO>

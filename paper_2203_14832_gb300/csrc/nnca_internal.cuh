@@ -319,6 +319,8 @@ struct Handle {
     // 64 targets (leaf, first target | targets << 16 | groups << 24, first record,
     // records), two targets per lane
     float4 *pw4 = nullptr;
+    float4 *pw8 = nullptr;        // the same for eight right-hand sides (4 float4 per pair; tensor-core forms)
+    int64_t near_pairs = 0;       // packed point pairs (ppk)
     int4 *near_items4 = nullptr;
     int n_near_items4 = 0;
     const char *m2l_fp32_unsupported = nullptr;   // why the FP32 M2L cannot run, or null
