@@ -86,7 +86,9 @@ constexpr int UP_CHUNK = 512;
 
 // w_B[b] = sum_a op_B[a][b] src[a]; op_B is m x r, row-major (m: the points of a
 // leaf or the pivots of the children). The TW warps of a team split the rows;
-// the lanes take 32 columns at a time (coalesced row segments).
+// the lanes take 32 columns at a time (coalesced row segments). blockIdx.y
+// selects a group of NR right-hand sides (xt and w advanced by NR rows per
+// group), so one launch serves every group of a pass.
 template <class T, int NR, int TW>
 __global__ void __launch_bounds__(UP_THREADS) k_upward(int64_t b0, int64_t b1, int leaf, const int32_t *cbeg,
                                                       const int32_t *cend, const int32_t *cch_beg,
@@ -94,6 +96,8 @@ __global__ void __launch_bounds__(UP_THREADS) k_upward(int64_t b0, int64_t b1, i
                                                       const int64_t *op_off, const T *op, const T *xt, int64_t N,
                                                       T *w, int64_t npiv, float *spk_w, const int32_t *spk_off,
                                                       float *spw = nullptr) {
+    xt += (int64_t)blockIdx.y * NR * N;
+    w += (int64_t)blockIdx.y * NR * npiv;
     constexpr int TEAMS = UP_THREADS / (32 * TW);
     // rows staged per chunk (halved for eight right-hand sides: the static shared memory)
     constexpr int CH = (TW == 1 ? 64 : UP_CHUNK) / (NR > 4 ? 2 : 1);
@@ -193,11 +197,13 @@ __global__ void __launch_bounds__(UP_THREADS) k_upward(int64_t b0, int64_t b1, i
 // u_{B_c} += C_{B_c P} u_P for the children of P: P's transfer C is m x r_P,
 // row-major, one row per pivot of P's children (in order). A block serves one
 // parent; its warps take rows 32 at a time, one row per lane, with u_P staged
-// in shared memory and UP_BATCH operator loads in flight per lane.
+// in shared memory and UP_BATCH operator loads in flight per lane. blockIdx.y
+// selects a group of NR right-hand sides (u advanced by NR rows per group).
 template <class T, int NR>
 __global__ void __launch_bounds__(UP_THREADS) k_l2l(int64_t p0, int64_t p1, const int32_t *cch_beg,
                                                    const int32_t *cch_end, const int32_t *piv_off,
                                                    const int64_t *op_off, const T *op, T *u, int64_t npiv) {
+    u += (int64_t)blockIdx.y * NR * npiv;
     __shared__ T su[NR][UP_CHUNK];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     constexpr int W = UP_THREADS / 32;
@@ -2458,13 +2464,16 @@ void pass_perm(Handle *h, const TO *xin, int64_t ld, double *xt, float *xt32, bo
 // a8, a9: P2M on the leaves, then M2M level by level (FP64 operators); spk_w,
 // spw: the float weights of the FP32 M2L's packed sources (one or M2L_RHS
 // right-hand sides), or null
+// groups: consecutive groups of NR right-hand sides served by the same launches
+// (spk_w and spw only with one group)
 template <int NR>
-void pass_up(Handle *h, const double *xt, double *w, float *spk_w, float *spw) {
+void pass_up(Handle *h, const double *xt, double *w, float *spk_w, float *spw, int groups = 1) {
     cudaStream_t s = h->stream;
     const int64_t N = h->n, npiv = h->npiv;
     const double *op = h->op;
     const int64_t lb = h->level_base[h->kappa], le = h->level_base[h->kappa + 1];
-    k_upward<double, NR, 1><<<grid_for(le - lb, UP_THREADS / 32), UP_THREADS, 0, s>>>(
+    NNCA_REQUIRE(groups >= 1 && (groups == 1 || (!spk_w && !spw)), NNCA_ERR_INTERNAL, "pass_up: bad group count");
+    k_upward<double, NR, 1><<<dim3(grid_for(le - lb, UP_THREADS / 32), groups), UP_THREADS, 0, s>>>(
         lb, le, 1, h->cbeg, h->cend, h->cch_beg, h->cch_end, h->piv_off, h->op_off, op, xt, N, w, npiv, spk_w,
         h->spk_off, spw);
     NNCA_LAUNCH_CHECK();
@@ -2472,7 +2481,7 @@ void pass_up(Handle *h, const double *xt, double *w, float *spk_w, float *spw) {
     for (int l = h->kappa - 1; l >= h->lmin; --l) {
         const int64_t b0 = h->level_base[l], b1 = h->level_base[l + 1];
         ++h->launches;
-        k_upward<double, NR, UP_THREADS / 32><<<grid_for(b1 - b0, 1), UP_THREADS, 0, s>>>(
+        k_upward<double, NR, UP_THREADS / 32><<<dim3(grid_for(b1 - b0, 1), groups), UP_THREADS, 0, s>>>(
             b0, b1, 0, h->cbeg, h->cend, h->cch_beg, h->cch_end, h->piv_off, h->op_off, op, xt, N, w, npiv, spk_w,
             h->spk_off, spw);
         NNCA_LAUNCH_CHECK();
@@ -2481,11 +2490,11 @@ void pass_up(Handle *h, const double *xt, double *w, float *spk_w, float *spw) {
 
 // a11: L2L, parents at level l - 1 push down to their children at level l
 template <int NR>
-void pass_l2l(Handle *h, double *u) {
+void pass_l2l(Handle *h, double *u, int groups = 1) {
     for (int l = h->lmin + 1; l <= h->kappa; ++l) {
         const int64_t p0 = h->level_base[l - 1], p1 = h->level_base[l];
         ++h->launches;
-        k_l2l<double, NR><<<grid_for(p1 - p0, 1), UP_THREADS, 0, h->stream>>>(p0, p1, h->cch_beg, h->cch_end,
+        k_l2l<double, NR><<<dim3(grid_for(p1 - p0, 1), groups), UP_THREADS, 0, h->stream>>>(p0, p1, h->cch_beg, h->cch_end,
                                                                               h->piv_off, h->op_off, h->op, u,
                                                                               h->npiv);
         NNCA_LAUNCH_CHECK();
@@ -2628,8 +2637,9 @@ void run_tc(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int mod
         if (far) {
             for (int r = 0; r < nr;) {
                 if (nr - r >= 2 * M2L_RHS) {
-                    pass_up<2 * M2L_RHS>(h, xt + r * N, w + r * npiv, nullptr, nullptr);
-                    r += 2 * M2L_RHS;
+                    const int ng = (nr - r) / (2 * M2L_RHS);   // every group of eight in the same launches
+                    pass_up<2 * M2L_RHS>(h, xt + r * N, w + r * npiv, nullptr, nullptr, ng);
+                    r += ng * 2 * M2L_RHS;
                 } else if (nr - r >= M2L_RHS) {
                     pass_up<M2L_RHS>(h, xt + r * N, w + r * npiv, nullptr, nullptr);
                     r += M2L_RHS;
@@ -2646,8 +2656,9 @@ void run_tc(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int mod
         if (far)
             for (int r = 0; r < nr;) {
                 if (nr - r >= 2 * M2L_RHS) {
-                    pass_l2l<2 * M2L_RHS>(h, u + r * npiv);
-                    r += 2 * M2L_RHS;
+                    const int ng = (nr - r) / (2 * M2L_RHS);
+                    pass_l2l<2 * M2L_RHS>(h, u + r * npiv, ng);
+                    r += ng * 2 * M2L_RHS;
                 } else if (nr - r >= M2L_RHS) {
                     pass_l2l<M2L_RHS>(h, u + r * npiv);
                     r += M2L_RHS;
