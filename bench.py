@@ -368,7 +368,9 @@ def run_ours(args):
     e2e_ok = bool(np.array_equal(yh_e2e, y32h))
 
     # roofline of the dominant kernel (M2L, FP32 evaluation): one rsqrt per pivot pair
-    calls = max(1, st_prof["pass_calls"])
+    # per product: the profiled region is exactly the K timed products (a product
+    # of several right-hand sides records one set of pass events per group)
+    calls = max(1, args.steps)
     m2l_ms = st_prof["pass_ms"][2] / calls
     pass_ms = [v / calls for v in st_prof["pass_ms"][:6]]
     peaks = measured_peaks()

@@ -95,9 +95,10 @@ __global__ void __launch_bounds__(UP_THREADS) k_upward(int64_t b0, int64_t b1, i
                                                       const int32_t *cch_end, const int32_t *piv_off,
                                                       const int64_t *op_off, const T *op, const T *xt, int64_t N,
                                                       T *w, int64_t npiv, float *spk_w, const int32_t *spk_off,
-                                                      float *spw = nullptr) {
+                                                      float *spw = nullptr, int64_t spw_stride = 0) {
     xt += (int64_t)blockIdx.y * NR * N;
     w += (int64_t)blockIdx.y * NR * npiv;
+    if (spw) spw += (int64_t)blockIdx.y * spw_stride;
     constexpr int TEAMS = UP_THREADS / (32 * TW);
     // rows staged per chunk (halved for eight right-hand sides: the static shared memory)
     constexpr int CH = (TW == 1 ? 64 : UP_CHUNK) / (NR > 4 ? 2 : 1);
@@ -2314,10 +2315,11 @@ void m2l_rhs_combine(Handle *h, double *u) {
 }
 
 template <int KIND>
-void launch_m2l_f32_rhs(Handle *h, double *u) {
+void launch_m2l_f32_rhs(Handle *h, double *u, const float4 *spw = nullptr) {
     if (!h->n_m2l_groups) return;
     M2lRhsTable<1> tab;
     tab.a[0] = m2l_rhs_args(h, u);
+    if (spw) tab.a[0].spw = spw;   // the packed weights of this group (else the handle's one-group buffer)
     launch_m2l_rhs_table<KIND, 1>(tab, nullptr, h->n_m2l_groups, h->m2l_next, h->stream);
     ++h->launches;
     m2l_rhs_combine(h, u);
@@ -2465,17 +2467,19 @@ void pass_perm(Handle *h, const TO *xin, int64_t ld, double *xt, float *xt32, bo
 // spw: the float weights of the FP32 M2L's packed sources (one or M2L_RHS
 // right-hand sides), or null
 // groups: consecutive groups of NR right-hand sides served by the same launches
-// (spk_w and spw only with one group)
+// (spk_w only with one group; the packed weights spw of group g at spw + g spw_stride)
 template <int NR>
-void pass_up(Handle *h, const double *xt, double *w, float *spk_w, float *spw, int groups = 1) {
+void pass_up(Handle *h, const double *xt, double *w, float *spk_w, float *spw, int groups = 1,
+             int64_t spw_stride = 0) {
     cudaStream_t s = h->stream;
     const int64_t N = h->n, npiv = h->npiv;
     const double *op = h->op;
     const int64_t lb = h->level_base[h->kappa], le = h->level_base[h->kappa + 1];
-    NNCA_REQUIRE(groups >= 1 && (groups == 1 || (!spk_w && !spw)), NNCA_ERR_INTERNAL, "pass_up: bad group count");
+    NNCA_REQUIRE(groups >= 1 && (groups == 1 || (!spk_w && (!spw || spw_stride > 0))), NNCA_ERR_INTERNAL,
+                 "pass_up: bad group count");
     k_upward<double, NR, 1><<<dim3(grid_for(le - lb, UP_THREADS / 32), groups), UP_THREADS, 0, s>>>(
         lb, le, 1, h->cbeg, h->cend, h->cch_beg, h->cch_end, h->piv_off, h->op_off, op, xt, N, w, npiv, spk_w,
-        h->spk_off, spw);
+        h->spk_off, spw, spw_stride);
     NNCA_LAUNCH_CHECK();
     ++h->launches;
     for (int l = h->kappa - 1; l >= h->lmin; --l) {
@@ -2483,7 +2487,7 @@ void pass_up(Handle *h, const double *xt, double *w, float *spk_w, float *spw, i
         ++h->launches;
         k_upward<double, NR, UP_THREADS / 32><<<dim3(grid_for(b1 - b0, 1), groups), UP_THREADS, 0, s>>>(
             b0, b1, 0, h->cbeg, h->cend, h->cch_beg, h->cch_end, h->piv_off, h->op_off, op, xt, N, w, npiv, spk_w,
-            h->spk_off, spw);
+            h->spk_off, spw, spw_stride);
         NNCA_LAUNCH_CHECK();
     }
 }
@@ -2709,9 +2713,83 @@ void ensure_tc_workspace(Handle *h) {
     }
 }
 
+// The FP32 form with ng groups of M2L_RHS right-hand sides (r0 .. r0 + 4 ng - 1):
+// the permutation, P2M/M2M and L2L of every group in the same launches (grid y
+// over the groups: the upper levels' few cells fill the GPU and each launch
+// serves all groups), the M2L one launch per group (its packed weights per group
+// in spw_multi), the near field in passes of eight right-hand sides where two
+// groups remain.
+template <int KIND, class TO>
+void run_quads(Handle *h, const void *x, void *y, int64_t ld, int64_t r0, int ng) {
+    cudaStream_t s = h->stream;
+    const int64_t N = h->n, npiv = h->npiv, nrt = (int64_t)ng * M2L_RHS;
+    double *xt = (double *)h->ws;
+    double *w = xt + nrt * N;
+    double *u = w + nrt * npiv;
+    float *xt32 = (float *)(u + nrt * npiv);
+    const TO *xin = (const TO *)x + r0 * ld;
+    TO *yout = (TO *)y + r0 * ld;
+    const int64_t sstride = 2 * M2L_RHS * h->n_spk_pairs;   // floats of one group's packed M2L weights
+    float *spw = reinterpret_cast<float *>(h->spw_multi);
+    prof_mark(h, 0);
+    for (int g = 0; g < ng; ++g)
+        pass_perm<M2L_RHS, TO>(h, xin + g * M2L_RHS * ld, ld, xt + g * M2L_RHS * N, xt32 + g * M2L_RHS * N, false);
+    prof_mark(h, 1);
+    if (npiv > 0) NNCA_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * nrt * npiv, s));
+    const bool far = h->lmin <= h->kappa && npiv > 0;
+    if (far) pass_up<M2L_RHS>(h, xt, w, nullptr, spw, ng, sstride);
+    prof_mark(h, 2);
+    if (far && h->n_m2l_tgt > 0)
+        for (int g = 0; g < ng; ++g)
+            launch_m2l_f32_rhs<KIND>(h, u + g * M2L_RHS * npiv, reinterpret_cast<const float4 *>(spw + g * sstride));
+    prof_mark(h, 3);
+    if (far) pass_l2l<M2L_RHS>(h, u, ng);
+    prof_mark(h, 4);
+    for (int g = 0; g < ng;) {
+        const int64_t o = (int64_t)g * M2L_RHS;
+        if (ng - g >= 2 && h->pw8) {
+            pass_near<true, 2 * M2L_RHS, KIND, TO>(h, u + o * npiv, xt + o * N, xt32 + o * N, yout + o * ld, ld);
+            g += 2;
+        } else {
+            pass_near<true, M2L_RHS, KIND, TO>(h, u + o * npiv, xt + o * N, xt32 + o * N, yout + o * ld, ld);
+            g += 1;
+        }
+    }
+    prof_mark(h, 5);
+}
+
+// buffers of the grouped FP32 passes: workspace rows, one set of packed M2L
+// weights per group, and the near field's weights of eight right-hand sides
+void ensure_quads(Handle *h, int ng) {
+    ensure_workspace(h, (int64_t)ng * M2L_RHS);
+    if (!h->spw_multi || h->spw_multi_groups < ng) {
+        if (h->spw_multi) dev_free(h, h->spw_multi);
+        h->spw_multi = nullptr;
+        const size_t n4 = (size_t)ng * (M2L_RHS / 2) * (size_t)h->n_spk_pairs;
+        h->spw_multi = dalloc<float4>(h, std::max<size_t>(n4, 1));
+        // the padding sources' weights must read as zero
+        NNCA_CUDA(cudaMemsetAsync(h->spw_multi, 0, std::max<size_t>(n4, 1) * sizeof(float4), h->stream));
+        h->spw_multi_groups = ng;
+    }
+    if (!h->pw8 && h->near_packed && h->n_near_items4) {
+        h->pw8 = dalloc<float4>(h, 4 * (size_t)h->near_pairs);
+        NNCA_CUDA(cudaMemsetAsync(h->pw8, 0, 4 * (size_t)h->near_pairs * sizeof(float4), h->stream));
+    }
+}
+
+constexpr int QUAD_GROUPS = 16;   // groups of M2L_RHS per grouped FP32 pass (64 right-hand sides)
+
 template <bool FP32, int KIND, class TO>
 void run_all(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld) {
     int64_t r0 = 0;
+    if (FP32 && kernel_is_radial(h->kp.kind) && nrhs >= 2 * M2L_RHS && !h->no_alloc) {
+        ensure_quads(h, (int)std::min<int64_t>(QUAD_GROUPS, nrhs / M2L_RHS));
+        while (nrhs - r0 >= 2 * M2L_RHS) {
+            const int ng = (int)std::min<int64_t>(QUAD_GROUPS, (nrhs - r0) / M2L_RHS);
+            run_quads<KIND, TO>(h, x, y, ld, r0, ng);
+            r0 += (int64_t)ng * M2L_RHS;
+        }
+    }
     while (r0 < nrhs) {
         if (nrhs - r0 >= 4) {
             run_chunk<FP32, 4, KIND, TO>(h, x, y, ld, r0);

@@ -319,7 +319,9 @@ struct Handle {
     // 64 targets (leaf, first target | targets << 16 | groups << 24, first record,
     // records), two targets per lane
     float4 *pw4 = nullptr;
-    float4 *pw8 = nullptr;        // the same for eight right-hand sides (4 float4 per pair; tensor-core forms)
+    float4 *pw8 = nullptr;        // the same for eight right-hand sides (4 float4 per pair)
+    float4 *spw_multi = nullptr;  // spw of each group of a grouped FP32 pass ([group][pairs][M2L_RHS / 2])
+    int spw_multi_groups = 0;
     int64_t near_pairs = 0;       // packed point pairs (ppk)
     int4 *near_items4 = nullptr;
     int n_near_items4 = 0;
