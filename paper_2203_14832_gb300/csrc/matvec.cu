@@ -2895,10 +2895,25 @@ void release_cross_plans(uint64_t uid) {
 }
 
 template <int KIND>
-void launch_cross(Handle *const *hs, const CrossList &L, double *const *u, cudaStream_t s) {
+void launch_cross(Handle *const *hs, const CrossList &L, double *const *u, const float4 *const *spw, cudaStream_t s) {
     M2lRhsTable<M2L_MULTI_MAX> tab;
-    for (size_t m = 0; m < L.members.size(); ++m) tab.a[m] = m2l_rhs_args(hs[L.members[m]], u[L.members[m]]);
+    for (size_t m = 0; m < L.members.size(); ++m) {
+        tab.a[m] = m2l_rhs_args(hs[L.members[m]], u[L.members[m]]);
+        tab.a[m].spw = spw[L.members[m]];
+    }
     launch_m2l_rhs_table<KIND, M2L_MULTI_MAX>(tab, L.gitems, L.nitems, L.next, s);
+}
+
+template <class TO>
+void near8_kind(Handle *h, const double *u, const double *xt, const float *xt32, TO *yout, int64_t ld) {
+    switch (h->kp.kind) {
+    case NNCA_K_INV_R: pass_near<true, 2 * M2L_RHS, NNCA_K_INV_R, TO>(h, u, xt, xt32, yout, ld); break;
+    case NNCA_K_LOG: pass_near<true, 2 * M2L_RHS, NNCA_K_LOG, TO>(h, u, xt, xt32, yout, ld); break;
+    case NNCA_K_GAUSS: pass_near<true, 2 * M2L_RHS, NNCA_K_GAUSS, TO>(h, u, xt, xt32, yout, ld); break;
+    case NNCA_K_MATERN: pass_near<true, 2 * M2L_RHS, NNCA_K_MATERN, TO>(h, u, xt, xt32, yout, ld); break;
+    case NNCA_K_PAPER_I: pass_near<true, 2 * M2L_RHS, NNCA_K_PAPER_I, TO>(h, u, xt, xt32, yout, ld); break;
+    default: pass_near<true, 2 * M2L_RHS, NNCA_K_PAPER_II, TO>(h, u, xt, xt32, yout, ld); break;
+    }
 }
 
 template <class TO>
@@ -2926,12 +2941,19 @@ void batch_fp32(Handle *const *hs, int count, const void *const *x, void *const 
             NNCA_CUDA(cudaStreamWaitEvent(s, join[i], 0));
         }
     };
+    // eight or more right-hand sides: passes of up to QUAD_GROUPS groups of four,
+    // with P2M/M2M and L2L of all groups in the same launches, the near field in
+    // groups of eight (as in the single product)
+    const int ngq = (int)std::min<int64_t>(QUAD_GROUPS, nrhs / M2L_RHS);
+    const bool grouped = ngq >= 2;
     for (int k = 0; k < count; ++k) {
-        ensure_workspace(hs[k], std::min<int64_t>(nrhs, 4));
+        if (grouped) ensure_quads(hs[k], ngq);
+        else ensure_workspace(hs[k], std::min<int64_t>(nrhs, 4));
         hs[k]->launches = 0;
     }
     CrossPlan &plan = cross_plan(hs, count);
-    std::vector<double *> uptr(count);
+    std::vector<double *> uptr(count), ug(count);
+    std::vector<const float4 *> spwg(count);
     int64_t r0 = 0;
     while (r0 < nrhs) {
         if (nrhs - r0 < M2L_RHS) {
@@ -2953,49 +2975,80 @@ void batch_fp32(Handle *const *hs, int count, const void *const *x, void *const 
             r0 += 1;
             continue;
         }
+        const int ng = grouped && nrhs - r0 >= 2 * M2L_RHS ? (int)std::min<int64_t>(ngq, (nrhs - r0) / M2L_RHS) : 1;
+        const int64_t nrt = (int64_t)ng * M2L_RHS;
         // permutation, P2M and M2M of every problem
         fork_all();
         for (int k = 0; k < count; ++k) {
             Handle *h = hs[k];
             h->stream = wk[k % nw];
             const int64_t N = h->n, npiv = h->npiv;
-            double *xt = (double *)h->ws, *w = xt + M2L_RHS * N, *u = w + M2L_RHS * npiv;
-            float *xt32 = (float *)(u + M2L_RHS * npiv);
+            double *xt = (double *)h->ws, *w = xt + nrt * N, *u = w + nrt * npiv;
+            float *xt32 = (float *)(u + nrt * npiv);
             uptr[k] = u;
-            pass_perm<M2L_RHS, TO>(h, (const TO *)x[k] + r0 * ld[k], ld[k], xt, xt32, false);
-            if (npiv > 0) NNCA_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * M2L_RHS * npiv, h->stream));
-            if (h->lmin <= h->kappa && npiv > 0) pass_up<M2L_RHS>(h, xt, w, nullptr, reinterpret_cast<float *>(h->spw));
+            const TO *xin = (const TO *)x[k] + r0 * ld[k];
+            for (int g = 0; g < ng; ++g)
+                pass_perm<M2L_RHS, TO>(h, xin + g * M2L_RHS * ld[k], ld[k], xt + g * M2L_RHS * N, xt32 + g * M2L_RHS * N,
+                                       false);
+            if (npiv > 0) NNCA_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * nrt * npiv, h->stream));
+            if (h->lmin <= h->kappa && npiv > 0) {
+                if (ng > 1)
+                    pass_up<M2L_RHS>(h, xt, w, nullptr, reinterpret_cast<float *>(h->spw_multi), ng,
+                                     2 * M2L_RHS * h->n_spk_pairs);
+                else
+                    pass_up<M2L_RHS>(h, xt, w, nullptr, reinterpret_cast<float *>(h->spw));
+            }
         }
         join_all();
-        // the M2L of all problems: one launch per kernel family over the cross-problem list
-        for (const CrossList &L : plan.lists) {
-            switch (L.kind) {
-            case NNCA_K_INV_R: launch_cross<NNCA_K_INV_R>(hs, L, uptr.data(), s); break;
-            case NNCA_K_LOG: launch_cross<NNCA_K_LOG>(hs, L, uptr.data(), s); break;
-            case NNCA_K_GAUSS: launch_cross<NNCA_K_GAUSS>(hs, L, uptr.data(), s); break;
-            case NNCA_K_MATERN: launch_cross<NNCA_K_MATERN>(hs, L, uptr.data(), s); break;
-            case NNCA_K_PAPER_I: launch_cross<NNCA_K_PAPER_I>(hs, L, uptr.data(), s); break;
-            default: launch_cross<NNCA_K_PAPER_II>(hs, L, uptr.data(), s); break;
+        // the M2L of all problems, group by group: one launch per kernel family over
+        // the cross-problem list, then the split pieces' combine of that group
+        for (int g = 0; g < ng; ++g) {
+            for (int k = 0; k < count; ++k) {
+                ug[k] = uptr[k] + (int64_t)g * M2L_RHS * hs[k]->npiv;
+                spwg[k] = ng > 1 ? hs[k]->spw_multi + (size_t)g * (M2L_RHS / 2) * (size_t)hs[k]->n_spk_pairs : hs[k]->spw;
             }
-            ++hs[L.members[0]]->launches;
+            for (const CrossList &L : plan.lists) {
+                switch (L.kind) {
+                case NNCA_K_INV_R: launch_cross<NNCA_K_INV_R>(hs, L, ug.data(), spwg.data(), s); break;
+                case NNCA_K_LOG: launch_cross<NNCA_K_LOG>(hs, L, ug.data(), spwg.data(), s); break;
+                case NNCA_K_GAUSS: launch_cross<NNCA_K_GAUSS>(hs, L, ug.data(), spwg.data(), s); break;
+                case NNCA_K_MATERN: launch_cross<NNCA_K_MATERN>(hs, L, ug.data(), spwg.data(), s); break;
+                case NNCA_K_PAPER_I: launch_cross<NNCA_K_PAPER_I>(hs, L, ug.data(), spwg.data(), s); break;
+                default: launch_cross<NNCA_K_PAPER_II>(hs, L, ug.data(), spwg.data(), s); break;
+                }
+                ++hs[L.members[0]]->launches;
+            }
+            for (int k = 0; k < count; ++k) {
+                Handle *h = hs[k];
+                if (h->lmin <= h->kappa && h->npiv > 0) {
+                    h->stream = s;
+                    m2l_rhs_combine(h, ug[k]);
+                }
+            }
         }
-        // split pieces, L2L and the near field of every problem
+        // L2L and the near field of every problem
         fork_all();
         for (int k = 0; k < count; ++k) {
             Handle *h = hs[k];
             h->stream = wk[k % nw];
             const int64_t N = h->n, npiv = h->npiv;
             double *xt = (double *)h->ws, *u = uptr[k];
-            float *xt32 = (float *)(u + M2L_RHS * npiv);
-            if (h->lmin <= h->kappa && npiv > 0) {
-                m2l_rhs_combine(h, u);
-                pass_l2l<M2L_RHS>(h, u);
+            float *xt32 = (float *)(u + nrt * npiv);
+            TO *yout = (TO *)y[k] + r0 * ld[k];
+            if (h->lmin <= h->kappa && npiv > 0) pass_l2l<M2L_RHS>(h, u, ng);
+            for (int g = 0; g < ng;) {
+                const int64_t o = (int64_t)g * M2L_RHS;
+                if (ng - g >= 2 && h->pw8) {
+                    near8_kind<TO>(h, u + o * npiv, xt + o * N, xt32 + o * N, yout + o * ld[k], ld[k]);
+                    g += 2;
+                } else {
+                    near4_kind<TO>(h, u + o * npiv, xt + o * N, xt32 + o * N, yout + o * ld[k], ld[k]);
+                    g += 1;
+                }
             }
-            near4_kind<TO>(h, u, xt, xt32, (TO *)y[k] + r0 * ld[k], ld[k]);
-            (void)N;
         }
         join_all();
-        r0 += M2L_RHS;
+        r0 += nrt;
     }
 }
 
