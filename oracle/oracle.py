@@ -301,6 +301,24 @@ def kernel_block(cfg: Config, X: np.ndarray, Y: np.ndarray) -> np.ndarray:
     return out
 
 
+def dense_matvec_pq(P: np.ndarray, Q: np.ndarray, x: np.ndarray, cfg: Config, rows=None,
+                    block: int = 512) -> np.ndarray:
+    """y = A x with A(i, j) = K(p_i, q_j), P and Q distinct point sets (Sec. 1, Eq. 1; no
+    diagonal rule: coincident p_i = q_j give the kernel's value at r = 0, 0 for the singular
+    kernels), on the rows `rows` of P (all if None), by blocks of rows."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    Q = np.ascontiguousarray(Q, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    one = x.ndim == 1
+    xx = x.reshape(1, -1) if one else x
+    idx = np.arange(P.shape[0]) if rows is None else np.asarray(rows, dtype=np.int64)
+    y = np.zeros((xx.shape[0], idx.shape[0]))
+    for i0 in range(0, idx.shape[0], block):
+        blk = kernel_block(cfg, P[idx[i0:i0 + block]], Q)
+        y[:, i0:i0 + block] = xx @ blk.T
+    return y[0] if one else y
+
+
 def entry_block(h: "H2", rows, cols) -> np.ndarray:
     """A(rows, cols) of a built tree (sorted positions), with the diagonal rule."""
     rows = np.asarray(rows, dtype=np.int64)

@@ -11,9 +11,13 @@
  *  2. Residual row: r_j = A(i, j) - sum_{l<k} u_l(i) v_l(j), the sum taken in
  *     ascending l as r_j <- fma(-u_l(i), v_l(j), r_j).
  *  3. Column pivot j* = argmax over unused columns of |r_j|, ties to the
- *     smallest j. If that maximum is exactly 0 the row carries nothing: it is
- *     marked used, the smallest unused row is taken next, and no cross is
- *     formed.
+ *     smallest j. If that maximum is 0, or at round-off level (at most 2^-44
+ *     times the row's largest entry max_j |A(i, j)|), the row carries nothing
+ *     new: it is marked used, the smallest unused row is taken next, and no
+ *     cross is formed. (A row that repeats a pivot row, as for two points at
+ *     the same location, has a residual of a few units in the last place;
+ *     taking it as a pivot would make the pivot block A_{tau sigma} of Eqs. 11
+ *     and 14 singular.)
  *  4. v = r * (1 / r_{j*});  u(i') = A(i', j*) - sum_{l<k} v_l(j*) u_l(i')
  *     (ascending l, fused as in 2).
  *  5. ||A^(k+1)||_F^2 = ||A^(k)||_F^2 + 2 sum_{l<k} (u_l.u)(v_l.v) + |u|^2 |v|^2,
@@ -70,9 +74,11 @@ long orc_aca(long m, long n, orc_entry_fn entry, const void *ctx, double eps,
     double frob2 = 0.0;
     long k = 0, i = 0;
     for (;;) {
-        /* 2. residual of row i */
+        /* 2. residual of row i (and the row's largest entry) */
+        double amax = 0.0;
         for (long j = 0; j < n; ++j) {
             double s = entry(ctx, i, j);
+            if (fabs(s) > amax) amax = fabs(s);
             for (long l = 0; l < k; ++l) s = fma(-U[l * m + i], V[l * n + j], s);
             r[j] = s;
         }
@@ -81,7 +87,7 @@ long orc_aca(long m, long n, orc_entry_fn entry, const void *ctx, double eps,
         double best = -1.0;
         for (long j = 0; j < n; ++j)
             if (!ucol[j] && fabs(r[j]) > best) { best = fabs(r[j]); jp = j; }
-        if (jp < 0 || best == 0.0) {
+        if (jp < 0 || best <= ldexp(amax, -44)) {
             urow[i] = 1;
             long nxt = -1;
             for (long t = 0; t < m; ++t) if (!urow[t]) { nxt = t; break; }

@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(ACA_T) k_aca(AcaArgs A) {
             for (int64_t l = t; l < k; l += ACA_T) sv_l[l] = A.pool[vtab[l] + n + i];
             if (t < d) xi[t] = A.xs[(int64_t)t * N + rows[i]];
             __syncthreads();
-            double best = -1.0;
+            double best = -1.0, amax = 0.0;
             int64_t bj = -1;
             for (int64_t j0 = t; j0 < n; j0 += 4 * ACA_T) {
                 double s[4];
@@ -257,6 +257,7 @@ __global__ void __launch_bounds__(ACA_T) k_aca(AcaArgs A) {
                         double y[4];
                         load_point(A.xs, N, d, cols[jj[u]], y);
                         s[u] = kern_exact(A.kp, xi, y);
+                        amax = fmax(amax, fabs(s[u]));
                     } else {
                         s[u] = 0.0;
                     }
@@ -278,8 +279,12 @@ __global__ void __launch_bounds__(ACA_T) k_aca(AcaArgs A) {
                 }
             }
             block_argmax(best, bj, redv, redi);
-            if (bj < 0 || best == 0.0) {
-                // the row carries nothing: mark it used and take the smallest unused row
+            int64_t aidx = 0;
+            block_argmax(amax, aidx, redv, redi);   // the row's largest entry (a maximum: order-free)
+            if (bj < 0 || best <= ldexp(amax, -44)) {
+                // the row carries nothing new (its residual is 0 or at round-off level, as
+                // for a point at the same location as a pivot): mark it used and take the
+                // smallest unused row
                 if (t == 0) urow[i] = 1;
                 __syncthreads();
                 int64_t ni = -1;

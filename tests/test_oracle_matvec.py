@@ -318,3 +318,45 @@ def test_passthrough_assembled_matrix(orc):
     assert rel(M, A) < 100 * cfg.aca_tol
     x = W.vector_normal(h.n, 8)
     assert rel(h.matvec(x)[h.perm], M @ x[h.perm]) < 1e-13
+
+
+def test_dense_pq_definition(orc):
+    """A(P, Q) x with distinct point sets: values fixed by hand (1/r and a Gaussian), the
+    coincident pair p_0 = q_0 giving 0 for the singular kernel and K(0) for the smooth one."""
+    P = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0]])
+    Q = np.array([[0.0, 0.0, 0.0], [0.0, 2.0, 0.0], [3.0, 0.0, 0.0]])
+    x = np.array([1.0, 2.0, 3.0])
+    c = orc.Config(d=3, kernel=orc.K_INV_R, kparam=(1.0, 0.0, 7.0, 0.0))
+    y = orc.dense_matvec_pq(P, Q, x, c)
+    assert abs(y[0] - (0.0 + 2.0 / 2.0 + 3.0 / 3.0)) < 1e-15
+    assert abs(y[1] - (1.0 + 2.0 / np.sqrt(5.0) + 3.0 / 2.0)) < 1e-15
+    g = orc.Config(d=3, kernel=orc.K_GAUSS, kparam=(1.0, 1.5, 7.0, 0.0))
+    yg = orc.dense_matvec_pq(P, Q, x, g)
+    e = lambda r2: np.exp(-r2 / (2 * 1.5 ** 2))
+    assert abs(yg[0] - (1.0 + 2 * e(4.0) + 3 * e(9.0))) < 1e-15
+    assert abs(yg[1] - (e(1.0) + 2 * e(5.0) + 3 * e(4.0))) < 1e-15
+    # rows and several right-hand sides agree with the full product
+    X = np.vstack([x, -x])
+    Y = orc.dense_matvec_pq(P, Q, X, c, rows=np.array([1]))
+    assert abs(Y[0, 0] - y[1]) < 1e-15 and abs(Y[1, 0] + y[1]) < 1e-15
+
+
+def test_pq_through_union(orc):
+    """A(P, Q) x as the P rows of the symmetric H^2 product of the union [P; Q] applied
+    to [0; x]: within the ACA tolerance of the dense P x Q product, and exactly the
+    union's own H^2 product (the embedding adds no error of its own)."""
+    rng = np.random.default_rng(11)
+    P = rng.uniform(0.0, 1.0, (1500, 3))
+    Q = np.vstack([rng.uniform(0.4, 1.4, (1200, 3)), P[:7]])     # overlapping box, 7 shared points
+    x = rng.standard_normal(Q.shape[0])
+    for kern, kp, eps in ((orc.K_INV_R, (1.0, 0.0, 0.0, 0.0), 1e-8), (orc.K_GAUSS, (1.0, 0.3, 1.0, 0.0), 1e-8)):
+        c = orc.Config(d=3, leaf_size=32, aca_tol=eps, kernel=kern, kparam=kp)
+        U = np.vstack([P, Q])
+        h = orc.H2(U, c)
+        yu = h.matvec(np.concatenate([np.zeros(P.shape[0]), x]))
+        yd = orc.dense_matvec_pq(P, Q, x, c)
+        assert np.linalg.norm(yu[:P.shape[0]] - yd) <= 10 * eps * np.linalg.norm(yd)
+        # the union's dense product on the same embedded vector, restricted to P: the
+        # P x Q block of the union matrix (the diagonal rule never applies there)
+        ydu = orc.dense_matvec(U, np.concatenate([np.zeros(P.shape[0]), x]), c)[:P.shape[0]]
+        assert np.linalg.norm(ydu - yd) <= 1e-14 * np.linalg.norm(yd)
