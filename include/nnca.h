@@ -158,12 +158,21 @@ typedef struct {
                                       serves both u_B and u_B'), else m2l_pairs */
 } nnca_stats;
 
-/* Build the H^2 representation of A(i, j) = K(p_i, q_j).
+/* Build the H^2 representation of A(i, j) = K(p_i, q_j) (Sec. 2, Sec. 3).
  *  cfg    host pointer; validated (d, leaf_size, eta2, aca_tol > 0, kernel,
  *         symmetric == 1).
  *  P      device pointer, nP points (layout), FP64, all finite.
- *  Q      device pointer or NULL; must equal P (or be NULL) with nQ == nP:
- *         general P != Q returns NNCA_ERR_UNSUPPORTED.
+ *  Q      device pointer or NULL. NULL, or Q == P with nQ == nP: the symmetric
+ *         case of Sec. 5 (A on P x P, the diagonal taking kparam[2]).
+ *         Otherwise nQ >= 1 points of Q in the same layout: the representation
+ *         is built on the union [P; Q] (nP + nQ < 2^31 points; P and Q may share
+ *         coordinates, which count as distinct points), and the products of the
+ *         handle return A(P, Q) x as the P rows of the union matrix applied to
+ *         [0; x]: the same nested bases and ACA tolerance, at the cost of the
+ *         union's size (the paper's separate incoming and outgoing bases, Eqs.
+ *         15-18, are not built). Such a handle serves nnca_matvec and
+ *         nnca_matvec_host only; the batched, no-allocation and gradient calls
+ *         return NNCA_ERR_UNSUPPORTED for it. Its statistics describe the union.
  *  out    host pointer that receives the handle (NULL on failure).
  * Synchronises `stream`. nP >= 1 and nP < 2^31. */
 nnca_status nnca_build(const nnca_config *cfg, const double *P, int64_t nP, const double *Q, int64_t nQ,
@@ -171,7 +180,9 @@ nnca_status nnca_build(const nnca_config *cfg, const double *P, int64_t nP, cons
 
 /* y = A~ x for nrhs right-hand sides. x, y: device pointers, element type
  * dtype (NNCA_F64 or NNCA_F32), column r at [r*ld .. r*ld + n). y is
- * overwritten. precision: NNCA_PREC_FP64 (all arithmetic in FP64),
+ * overwritten. For a P != Q handle x holds nQ entries and y nP entries per
+ * column (ld >= max(nP, nQ)), and the call also uses a workspace of two union
+ * vectors per right-hand side. precision: NNCA_PREC_FP64 (all arithmetic in FP64),
  * NNCA_PREC_FP32 (kernel evaluations and contractions in FP32 with
  * cell-relative coordinates and compensated accumulation across cells), or a
  * tensor-core form (NNCA_PREC_TF32X3, NNCA_PREC_TF32, NNCA_PREC_BF16).

@@ -161,9 +161,11 @@ nnca_status nnca_build(const nnca_config *cfg, const double *P, int64_t nP, cons
         return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_build: unknown m2l_form");
     if (cfg->m2l_item_targets != 0 && (cfg->m2l_item_targets < 32 || cfg->m2l_item_targets > 256))
         return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_build: m2l_item_targets must be 0 or 32..256");
-    if (Q && (Q != P || nQ != nP))
-        return fail(nullptr, NNCA_ERR_UNSUPPORTED, "nnca_build: P != Q is not supported (pass Q = NULL or Q = P)");
-    if (!is_device_ptr(P)) return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_build: P is not device memory");
+    const bool pq = Q && (Q != P || nQ != nP);
+    if (pq && (nQ < 1 || nP + nQ >= (1ll << 31)))
+        return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_build: need 1 <= nQ and nP + nQ < 2^31");
+    if (!is_device_ptr(P) || (pq && !is_device_ptr(Q)))
+        return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_build: P and Q must be device memory");
 
     static std::atomic<uint64_t> next_uid{1};
     nnca_handle_s *h = new nnca_handle_s();
@@ -186,7 +188,38 @@ nnca_status nnca_build(const nnca_config *cfg, const double *P, int64_t nP, cons
             h->kp.hf = (float)cfg->kparam[1];
         h->dev_status = dalloc<unsigned>(h, 1);
         NNCA_CUDA(cudaMemsetAsync(h->dev_status, 0, sizeof(unsigned), h->stream));
-        build_tree(h, P, layout);
+        if (pq) {
+            // the union [P; Q] in the caller's layout, kept only for the tree build
+            h->pq = true;
+            h->n_rows = nP;
+            h->n_cols = nQ;
+            h->n = nP + nQ;
+            const int64_t n = h->n, d = cfg->d;
+            double *U = nullptr;
+            NNCA_CUDA(cudaMalloc(&U, sizeof(double) * n * d));
+            if (layout == NNCA_LAYOUT_AOS) {
+                NNCA_CUDA(cudaMemcpyAsync(U, P, sizeof(double) * nP * d, cudaMemcpyDeviceToDevice, h->stream));
+                NNCA_CUDA(cudaMemcpyAsync(U + nP * d, Q, sizeof(double) * nQ * d, cudaMemcpyDeviceToDevice, h->stream));
+            } else {
+                for (int64_t k = 0; k < d; ++k) {
+                    NNCA_CUDA(cudaMemcpyAsync(U + k * n, P + k * nP, sizeof(double) * nP, cudaMemcpyDeviceToDevice,
+                                              h->stream));
+                    NNCA_CUDA(cudaMemcpyAsync(U + k * n + nP, Q + k * nQ, sizeof(double) * nQ,
+                                              cudaMemcpyDeviceToDevice, h->stream));
+                }
+            }
+            try {
+                build_tree(h, U, layout);
+            } catch (...) {
+                cudaStreamSynchronize(h->stream);
+                cudaFree(U);
+                throw;
+            }
+            NNCA_CUDA(cudaStreamSynchronize(h->stream));
+            NNCA_CUDA(cudaFree(U));
+        } else {
+            build_tree(h, P, layout);
+        }
         NNCA_REQUIRE(!(read_status(h) & DEV_BAD_INDEX), NNCA_ERR_INVALID_ARG, "nnca_build: non-finite coordinates");
         h->stats.build_ms[0] = ms_since(t0);
         auto t1 = std::chrono::steady_clock::now();
@@ -238,12 +271,39 @@ nnca_status nnca_build(const nnca_config *cfg, const double *P, int64_t nP, cons
     return NNCA_OK;
 }
 
+namespace {
+// P != Q: y (rows of n_rows at pitch ld) = the P rows of the product of the union
+// matrix with [0; x] (x: rows of n_cols at pitch ld). kind: the copies' direction
+// for x and y (device or host buffers).
+void pq_matvec(Handle *h, const void *x, void *y, int64_t nrhs, int64_t ld, int dtype, int precision, bool host) {
+    cudaStream_t s = h->stream;
+    const size_t es = dtype == NNCA_F64 ? 8 : 4;
+    const int64_t n = h->n, np = h->n_rows, nq = h->n_cols;
+    const size_t need = 2 * (size_t)n * nrhs * es;
+    if (h->pq_buf_bytes < need) {
+        if (h->pq_buf) dev_free(h, h->pq_buf);
+        h->pq_buf = nullptr;
+        h->pq_buf = dev_alloc(h, need);
+        h->pq_buf_bytes = need;
+    }
+    char *xb = (char *)h->pq_buf;
+    char *yb = xb + (size_t)n * nrhs * es;
+    NNCA_CUDA(cudaMemset2DAsync(xb, n * es, 0, np * es, nrhs, s));
+    NNCA_CUDA(cudaMemcpy2DAsync(xb + np * es, n * es, x, ld * es, nq * es, nrhs,
+                                host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    matvec(h, xb, yb, nrhs, n, dtype, precision);
+    NNCA_CUDA(cudaMemcpy2DAsync(y, ld * es, yb, n * es, np * es, nrhs,
+                                host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+}
+}  // namespace
+
 nnca_status nnca_matvec(nnca_handle h, const void *x, void *y, int64_t nrhs, int64_t ld, int dtype, int precision,
                         void *stream) {
     if (!h) return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_matvec: NULL handle");
     if (!x || !y) return fail(h, NNCA_ERR_INVALID_ARG, "nnca_matvec: NULL x or y");
     if (nrhs < 1) return fail(h, NNCA_ERR_INVALID_ARG, "nnca_matvec: nrhs must be >= 1");
-    if (ld < h->n) return fail(h, NNCA_ERR_INVALID_ARG, "nnca_matvec: ld must be >= n");
+    if (ld < (h->pq ? std::max(h->n_rows, h->n_cols) : h->n))
+        return fail(h, NNCA_ERR_INVALID_ARG, "nnca_matvec: ld must be >= n (>= max(nP, nQ) for P != Q)");
     if (dtype != NNCA_F64 && dtype != NNCA_F32) return fail(h, NNCA_ERR_INVALID_ARG, "nnca_matvec: unknown dtype");
     if (precision < NNCA_PREC_FP64 || precision > NNCA_PREC_BF16)
         return fail(h, NNCA_ERR_INVALID_ARG, "nnca_matvec: unknown precision");
@@ -251,7 +311,8 @@ nnca_status nnca_matvec(nnca_handle h, const void *x, void *y, int64_t nrhs, int
         return fail(h, NNCA_ERR_INVALID_ARG, "nnca_matvec: x and y must be device memory");
     try {
         h->stream = (cudaStream_t)stream;
-        matvec(h, x, y, nrhs, ld, dtype, precision);
+        if (h->pq) pq_matvec(h, x, y, nrhs, ld, dtype, precision, false);
+        else matvec(h, x, y, nrhs, ld, dtype, precision);
         h->stats.launches_per_product = h->launches;
     } catch (const Error &e) {
         return fail(h, e.status, e.what());
@@ -306,6 +367,7 @@ nnca_status nnca_matvec_batch(const nnca_handle *hs, int count, const void *cons
         if (!hs[k]) return fail(nullptr, NNCA_ERR_INVALID_ARG, at + "NULL handle");
         if (!seen.insert(hs[k]).second) return fail(nullptr, NNCA_ERR_INVALID_ARG, at + "handle repeated");
         if (!x[k] || !y[k]) return fail(nullptr, NNCA_ERR_INVALID_ARG, at + "NULL x or y");
+        if (hs[k]->pq) return fail(nullptr, NNCA_ERR_UNSUPPORTED, at + "P != Q handles take nnca_matvec");
         if (ld[k] < hs[k]->n) return fail(nullptr, NNCA_ERR_INVALID_ARG, at + "ld below n");
         if (!is_device_ptr(x[k]) || !is_device_ptr(y[k]))
             return fail(nullptr, NNCA_ERR_INVALID_ARG, at + "x and y must be device memory");
@@ -345,11 +407,21 @@ nnca_status nnca_matvec_host(nnca_handle h, const void *x_host, void *y_host, in
                              int precision, void *stream) {
     if (!h) return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_matvec_host: NULL handle");
     if (!x_host || !y_host) return fail(h, NNCA_ERR_INVALID_ARG, "nnca_matvec_host: NULL x or y");
-    if (nrhs < 1 || ld < h->n) return fail(h, NNCA_ERR_INVALID_ARG, "nnca_matvec_host: bad nrhs or ld");
+    if (nrhs < 1 || ld < (h->pq ? std::max(h->n_rows, h->n_cols) : h->n))
+        return fail(h, NNCA_ERR_INVALID_ARG, "nnca_matvec_host: bad nrhs or ld");
     if (dtype != NNCA_F64 && dtype != NNCA_F32) return fail(h, NNCA_ERR_INVALID_ARG, "nnca_matvec_host: unknown dtype");
+    if (precision < NNCA_PREC_FP64 || precision > NNCA_PREC_BF16)
+        return fail(h, NNCA_ERR_INVALID_ARG, "nnca_matvec_host: unknown precision");
     try {
         cudaStream_t s = (cudaStream_t)stream;
         h->stream = s;
+        if (h->pq) {
+            pq_matvec(h, x_host, y_host, nrhs, ld, dtype, precision, true);
+            NNCA_CUDA(cudaStreamSynchronize(s));
+            NNCA_REQUIRE(!(read_status(h) & (DEV_WAIT_TIMEOUT | DEV_BAD_INDEX)), NNCA_ERR_INTERNAL,
+                         "nnca_matvec_host: a device-side check of the product failed");
+            return NNCA_OK;
+        }
         const size_t es = dtype == NNCA_F64 ? 8 : 4;
         const size_t need = 2 * (size_t)h->n * nrhs * es;
         if (h->host_stage_bytes < need) {
@@ -376,6 +448,7 @@ nnca_status nnca_matvec_host(nnca_handle h, const void *x_host, void *y_host, in
 nnca_status nnca_gradient(nnca_handle h, const double *x, const double *g, int64_t nrhs, int64_t ld, double *grad_p,
                           double *grad_h, void *stream) {
     if (!h) return fail(nullptr, NNCA_ERR_INVALID_ARG, "nnca_gradient: NULL handle");
+    if (h->pq) return fail(h, NNCA_ERR_UNSUPPORTED, "nnca_gradient: the gradient is built for P = Q");
     if (!x || !g || !grad_p) return fail(h, NNCA_ERR_INVALID_ARG, "nnca_gradient: NULL x, g or grad_p");
     if (nrhs < 1 || ld < h->n) return fail(h, NNCA_ERR_INVALID_ARG, "nnca_gradient: bad nrhs or ld");
     if (!is_device_ptr(x) || !is_device_ptr(g) || !is_device_ptr(grad_p) || (grad_h && !is_device_ptr(grad_h)))

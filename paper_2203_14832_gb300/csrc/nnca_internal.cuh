@@ -375,6 +375,13 @@ struct Handle {
     size_t tc_ws_bytes = 0;
     void *host_stage = nullptr;   // device buffers for nnca_matvec_host
     size_t host_stage_bytes = 0;
+    // P != Q: the representation is built on the union [P; Q] (n = n_rows + n_cols
+    // points, caller order P then Q); a product takes x on Q, embeds it as [0; x],
+    // runs the symmetric product and returns its rows on P
+    bool pq = false;
+    int64_t n_rows = 0, n_cols = 0;
+    void *pq_buf = nullptr;
+    size_t pq_buf_bytes = 0;
 
     // per-pass profiling of the product
     bool profile = false;

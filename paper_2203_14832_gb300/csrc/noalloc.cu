@@ -58,6 +58,10 @@ extern "C" nnca_status nnca_matvec_noalloc(nnca_handle hh, const void *x, void *
                                            int precision, void *stream) {
     nnca::Handle *h = static_cast<nnca::Handle *>(hh);
     if (!h) return NNCA_ERR_INVALID_ARG;
+    if (h->pq) {
+        h->last_error = "nnca_matvec_noalloc: P != Q handles take nnca_matvec";
+        return NNCA_ERR_UNSUPPORTED;
+    }
     if (!x || !y || ld < h->n || (dtype != NNCA_F64 && dtype != NNCA_F32) ||
         (precision != NNCA_PREC_FP64 && precision != NNCA_PREC_FP32)) {
         h->last_error = "nnca_matvec_noalloc: invalid x, y, ld, dtype or precision";

@@ -135,15 +135,20 @@ def nnca_last_error(handle=None) -> str:
     return lib().nnca_last_error(handle).decode(errors="replace")
 
 
-def nnca_build(cfg: Config, P, stream=None, layout: int = LAYOUT_AOS):
+def nnca_build(cfg: Config, P, stream=None, layout: int = LAYOUT_AOS, Q=None):
     """Build the H^2 representation of the points P (a CUDA float64 tensor, n x d for the
-    AoS layout). Returns the opaque handle (a ctypes void pointer)."""
+    AoS layout), or of A(P, Q) when Q (the same kind of tensor) is given. Returns the
+    opaque handle (a ctypes void pointer)."""
     import torch
     assert isinstance(P, torch.Tensor) and P.is_cuda and P.dtype == torch.float64 and P.is_contiguous()
     n = P.shape[0] if layout == LAYOUT_AOS else P.shape[1]
+    qp, nq = None, 0
+    if Q is not None:
+        assert isinstance(Q, torch.Tensor) and Q.is_cuda and Q.dtype == torch.float64 and Q.is_contiguous()
+        qp, nq = Q.data_ptr(), (Q.shape[0] if layout == LAYOUT_AOS else Q.shape[1])
     c = cfg.c()
     out = C.c_void_p()
-    st = lib().nnca_build(C.byref(c), P.data_ptr(), n, None, 0, layout, _stream_ptr(stream), C.byref(out))
+    st = lib().nnca_build(C.byref(c), P.data_ptr(), n, qp, nq, layout, _stream_ptr(stream), C.byref(out))
     _check(st, None)
     return out
 
@@ -238,32 +243,56 @@ def nnca_export(handle, what: str) -> np.ndarray:
 
 
 class H2:
-    """Convenience owner of a handle: build on construction, destroy on close/del."""
+    """Convenience owner of a handle: build on construction, destroy on close/del.
+    With Q, the handle represents A(P, Q): products take x on Q (m entries) and
+    return y on P (n entries)."""
 
-    def __init__(self, P, cfg: Config, stream=None):
+    def __init__(self, P, cfg: Config, stream=None, Q=None):
         import torch
         if not isinstance(P, torch.Tensor):
             P = torch.as_tensor(np.ascontiguousarray(P, dtype=np.float64), device="cuda")
+        if Q is not None and not isinstance(Q, torch.Tensor):
+            Q = torch.as_tensor(np.ascontiguousarray(Q, dtype=np.float64), device="cuda")
         self.P = P.contiguous()
+        self.Q = Q.contiguous() if Q is not None else None
         self.cfg = cfg
         self.n = self.P.shape[0]
-        self.handle = nnca_build(cfg, self.P, stream)
+        self.m = self.Q.shape[0] if self.Q is not None else self.n
+        self.handle = nnca_build(cfg, self.P, stream, Q=self.Q)
 
     def matvec(self, x, precision: int = PREC_FP64, out=None, stream=None):
-        """x: CUDA tensor (n,) or (nrhs, n); returns y of the same shape and dtype."""
+        """x: CUDA tensor (m,) or (nrhs, m); returns y, (n,) or (nrhs, n), of x's dtype."""
         import torch
         x = x.contiguous()
         nrhs = 1 if x.dim() == 1 else x.shape[0]
-        y = out if out is not None else torch.empty_like(x)
-        nnca_matvec(self.handle, x, y, nrhs, self.n, precision, stream)
-        return y
+        assert x.shape[-1] == self.m
+        shape = (self.n,) if x.dim() == 1 else (nrhs, self.n)
+        if self.m == self.n:
+            y = out if out is not None else torch.empty_like(x)
+            nnca_matvec(self.handle, x, y, nrhs, self.n, precision, stream)
+            return y
+        ld = max(self.n, self.m)
+        xp = torch.zeros((nrhs, ld), dtype=x.dtype, device=x.device)
+        xp[:, :self.m] = x.reshape(nrhs, self.m)
+        yp = torch.empty((nrhs, ld), dtype=x.dtype, device=x.device)
+        nnca_matvec(self.handle, xp, yp, nrhs, ld, precision, stream)
+        y = yp[:, :self.n].reshape(shape)
+        if out is not None:
+            out.copy_(y)
+            return out
+        return y.contiguous()
 
     def matvec_host(self, x: np.ndarray, precision: int = PREC_FP64, stream=None) -> np.ndarray:
         x = np.ascontiguousarray(x)
         nrhs = 1 if x.ndim == 1 else x.shape[0]
-        y = np.empty_like(x)
-        nnca_matvec_host(self.handle, x, y, nrhs, self.n, precision, stream)
-        return y
+        assert x.shape[-1] == self.m
+        ld = max(self.n, self.m)
+        xp = np.zeros((nrhs, ld), dtype=x.dtype)
+        xp[:, :self.m] = x.reshape(nrhs, self.m)
+        yp = np.empty((nrhs, ld), dtype=x.dtype)
+        nnca_matvec_host(self.handle, xp, yp, nrhs, ld, precision, stream)
+        y = yp[:, :self.n]
+        return np.ascontiguousarray(y[0] if x.ndim == 1 else y)
 
     def stats(self) -> dict:
         return nnca_get_stats(self.handle)
