@@ -1434,6 +1434,13 @@ void build_finish(Handle *h) {
             ItemSet sym;
             build_plan(M2L_SYM_CAP, 1, h->sym_plan, h->sym_plan_sh, h->n_sym_plan, sroff);
             make_items(h->sym_plan, h->n_sym_plan, sroff, true, splan, sym);
+            {
+                // the pair loop's form (see m2l_sym_pairs): unrolled when the staged
+                // records hold at least a chunk of source pairs on average
+                int64_t pairs = 0;
+                for (const int4 &r : splan) pairs += (r.z >> 11) & 0x7ff;
+                h->sym_unroll = !splan.empty() && pairs >= (int64_t)M2L_CHUNK_PAIRS * (int64_t)splan.size();
+            }
             std::vector<int> icol(sym.items.size());
             std::vector<std::vector<int32_t>> per_cell(nc);
             int64_t ncol = 0;

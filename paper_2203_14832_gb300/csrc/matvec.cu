@@ -522,6 +522,7 @@ constexpr int M2L_GROUP_THREADS = 32 * M2L_GROUP_WARPS;
 
 constexpr int M2L_STAGE_AHEAD = M2L_STAGE_BUFS - 2;
 constexpr int M2L_FOLD = 8;   // couples of source pairs per lane between folds into the compensated totals
+static_assert(2 * M2L_FOLD == M2L_CHUNK_PAIRS, "chunk size shared with the build's choice of the pair loop");
 constexpr int M2L_FOLD_RHS = 4;   // the same with M2L_RHS right-hand sides (one chain per right-hand side)
 
 struct M2lGroupSmem {
@@ -687,17 +688,15 @@ __device__ __forceinline__ f2 group_f(const KParams &kp, const ulonglong2 &A, co
 }
 
 // the source pairs q0, q0 + step, ... below q1 (pairs taken two at a time) of one
-// staged cell against two targets; FULL: the whole warp, step 2. At most
-// M2L_FOLD steps (one chunk), unrolled with a warp-uniform exit.
+// staged cell against two targets. FULL (the whole warp, step 2): at most
+// M2L_FOLD steps (one chunk), unrolled with a warp-uniform exit; otherwise
+// (lane groups splitting the pairs of small items) a counted loop, which keeps
+// the kernel's code small for the clustered inputs that run that path most.
 template <int KIND, int FULL>
 __device__ __forceinline__ void m2l_cell_pairs(const KParams &kp, const float4 (*src)[2], int q0, int q1, f2 xa, f2 ya,
                                                f2 za, f2 xb, f2 yb, f2 zb, f2 &a0, f2 &a1, f2 &b0, f2 &b1,
                                                int step = 2) {
-    if (FULL) step = 2;
-    int q = q0;
-#pragma unroll
-    for (int k = 0; k < M2L_FOLD; ++k, q += step) {
-        if (q >= q1) break;
+    auto body = [&](int q) {
         const ulonglong2 A0 = *reinterpret_cast<const ulonglong2 *>(&src[q][0]);
         const ulonglong2 B0 = *reinterpret_cast<const ulonglong2 *>(&src[q][1]);
         const ulonglong2 A1 = *reinterpret_cast<const ulonglong2 *>(&src[q + 1][0]);
@@ -706,6 +705,15 @@ __device__ __forceinline__ void m2l_cell_pairs(const KParams &kp, const float4 (
         b0 = group_pair<KIND>(kp, A0, B0, xb, yb, zb, b0);
         a1 = group_pair<KIND>(kp, A1, B1, xa, ya, za, a1);
         b1 = group_pair<KIND>(kp, A1, B1, xb, yb, zb, b1);
+    };
+    if (FULL) {
+#pragma unroll
+        for (int k = 0; k < M2L_FOLD; ++k) {
+            if (q0 + 2 * k >= q1) break;
+            body(q0 + 2 * k);
+        }
+    } else {
+        for (int q = q0; q < q1; q += step) body(q);
     }
 }
 
@@ -1935,19 +1943,18 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS) k_m2l_group_rhs(const __gri
 
 // the source pairs q0, q0 + step, ... below q1 (two at a time) of one staged
 // segment against two targets: row sums into a*, b*; the column values
-// f_a w_a + f_b w_b of each source pair into crow[q]. A chunk takes at most
-// M2L_FOLD steps (q1 - q0 <= M2L_FOLD * step): the loop is unrolled that far
-// with a warp-uniform exit, which measured faster than a counted loop (M2L of
-// the 1M-point 1/r workload 5.39 -> 5.15 ms).
-template <int KIND, int FULL>
+// f_a w_a + f_b w_b of each source pair into crow[q]. FULL (the whole warp,
+// step 2) with UNR: a chunk takes at most M2L_FOLD steps, and the loop is
+// unrolled that far with a warp-uniform exit; otherwise a counted loop. The
+// unrolled form is faster on trees with long staged records (M2L of the
+// 1M-point 1/r workload 5.39 -> 5.15 ms) and slower on trees of tiny cells
+// (262k-point Chebyshev grid 12.8 -> 16.5 ms; unrolling the lane-group path of
+// small items as well took it to 21.4 ms), so the build picks UNR per handle.
+template <int KIND, int FULL, int UNR = 1>
 __device__ __forceinline__ void m2l_sym_pairs(const KParams &kp, const float4 (*src)[2], int q0, int q1, f2 xa, f2 ya,
                                               f2 za, f2 xb, f2 yb, f2 zb, f2 WA, f2 WB, f2 *crow, f2 &a0, f2 &a1,
                                               f2 &b0, f2 &b1, int step = 2) {
-    if (FULL) step = 2;
-    int q = q0;
-#pragma unroll
-    for (int k = 0; k < M2L_FOLD; ++k, q += step) {
-        if (q >= q1) break;
+    auto body = [&](int q) {
         const ulonglong2 A0 = *reinterpret_cast<const ulonglong2 *>(&src[q][0]);
         const ulonglong2 B0 = *reinterpret_cast<const ulonglong2 *>(&src[q][1]);
         const ulonglong2 A1 = *reinterpret_cast<const ulonglong2 *>(&src[q + 1][0]);
@@ -1960,6 +1967,17 @@ __device__ __forceinline__ void m2l_sym_pairs(const KParams &kp, const float4 (*
         b1 = f2_fma(fb1, B1.y, b1);
         crow[q] = f2_fma(fb0, WB, f2_mul(fa0, WA));
         crow[q + 1] = f2_fma(fb1, WB, f2_mul(fa1, WA));
+    };
+    if (FULL && !UNR) {
+        for (int q = q0; q < q1; q += 2) body(q);
+    } else if (FULL) {
+#pragma unroll
+        for (int k = 0; k < M2L_FOLD; ++k) {
+            if (q0 + 2 * k >= q1) break;
+            body(q0 + 2 * k);
+        }
+    } else {
+        for (int q = q0; q < q1; q += step) body(q);
     }
 }
 
@@ -2010,7 +2028,7 @@ __device__ __forceinline__ void m2l_sym_columns_any(const f2 *cbuf, int rs, int 
     m2l_sym_columns<0>(cbuf, rs, L, np2, lane, out);
 }
 
-template <int KIND>
+template <int KIND, int UNR>
 __global__ void __launch_bounds__(M2L_GROUP_THREADS, KIND == NNCA_K_INV_R ? 5 : 4) k_m2l_sym(KParams kp, const int4 *items, int nitems,
                                                              int *next_item, const int4 *plan, const float4 *plan_sh,
                                                              const int32_t *cch_beg, const int32_t *cch_end,
@@ -2105,7 +2123,7 @@ __global__ void __launch_bounds__(M2L_GROUP_THREADS, KIND == NNCA_K_INV_R ? 5 : 
                         f2 a0 = 0ull, a1 = 0ull, b0 = 0ull, b1 = 0ull;
                         f2 *crow = cbuf + ti * rs - c0;
                         if (G == 1)
-                            m2l_sym_pairs<KIND, 1>(kp, S.src[b], c0, c1, xa, ya, za, xb, yb, zb, WA, WB, crow, a0, a1, b0,
+                            m2l_sym_pairs<KIND, 1, UNR>(kp, S.src[b], c0, c1, xa, ya, za, xb, yb, zb, WA, WB, crow, a0, a1, b0,
                                                    b1);
                         else
                             m2l_sym_pairs<KIND, 0>(kp, S.src[b], c0 + 2 * grp, c1, xa, ya, za, xb, yb, zb, WA, WB, crow,
@@ -2234,23 +2252,29 @@ void launch_m2l_f32(Handle *h, double *u) {
 
 // the symmetric form: rows by k_m2l_sym (and the split pieces' combine), then
 // the column sums of every cell
-template <int KIND>
-void launch_m2l_sym(Handle *h, const double *w, double *u) {
+template <int KIND, int UNR>
+void launch_m2l_sym_kernel(Handle *h, const double *w, double *u) {
     const int smem = (int)sizeof(M2lSymSmem);
-    NNCA_CUDA(cudaFuncSetAttribute(k_m2l_sym<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    NNCA_CUDA(cudaFuncSetAttribute(k_m2l_sym<KIND, UNR>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int dev = 0, nsm = 152, per_sm = 1;
     NNCA_CUDA(cudaGetDevice(&dev));
     NNCA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    NNCA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_m2l_sym<KIND, UNR>, M2L_GROUP_THREADS, smem));
+    const unsigned g = (unsigned)std::min<int64_t>(h->n_sym_items, (int64_t)nsm * std::max(1, per_sm));
+    NNCA_CUDA(cudaMemsetAsync(h->m2l_next, 0, sizeof(int), h->stream));
+    k_m2l_sym<KIND, UNR><<<g, M2L_GROUP_THREADS, smem, h->stream>>>(
+        h->kp, h->sym_items, h->n_sym_items, h->m2l_next, h->sym_plan, h->sym_plan_sh, h->cch_beg, h->cch_end,
+        h->prange, h->pv4, h->chi4, h->clo4, h->spk, w, h->sym_item_part, h->sym_item_col, h->sym_parts, u,
+        h->sym_col, h->dev_status);
+    NNCA_LAUNCH_CHECK();
+    ++h->launches;
+}
+
+template <int KIND>
+void launch_m2l_sym(Handle *h, const double *w, double *u) {
     if (h->n_sym_items) {
-        NNCA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_m2l_sym<KIND>, M2L_GROUP_THREADS, smem));
-        const unsigned g = (unsigned)std::min<int64_t>(h->n_sym_items, (int64_t)nsm * std::max(1, per_sm));
-        NNCA_CUDA(cudaMemsetAsync(h->m2l_next, 0, sizeof(int), h->stream));
-        k_m2l_sym<KIND><<<g, M2L_GROUP_THREADS, smem, h->stream>>>(
-            h->kp, h->sym_items, h->n_sym_items, h->m2l_next, h->sym_plan, h->sym_plan_sh, h->cch_beg, h->cch_end,
-            h->prange, h->pv4, h->chi4, h->clo4, h->spk, w, h->sym_item_part, h->sym_item_col, h->sym_parts, u,
-            h->sym_col, h->dev_status);
-        NNCA_LAUNCH_CHECK();
-        ++h->launches;
+        if (h->sym_unroll) launch_m2l_sym_kernel<KIND, 1>(h, w, u);
+        else launch_m2l_sym_kernel<KIND, 0>(h, w, u);
     }
     if (h->n_sym_split) {
         k_m2l_combine<<<(unsigned)std::min(h->n_sym_split, 152 * 16), 256, 0, h->stream>>>(h->sym_split, h->n_sym_split,

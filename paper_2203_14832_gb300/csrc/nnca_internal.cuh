@@ -190,6 +190,9 @@ constexpr int M2L_RHS = 4;
 // M2L_SYM_CAP padded sources (so the per-warp column sums of the rounds in
 // flight fit in shared memory beside the staged sources).
 constexpr int M2L_SYM_CAP = 256;
+// source pairs of one chunk of the FP32 M2L pair loop when a whole warp shares it
+// (two pairs per step, M2L_FOLD steps between folds into the compensated totals)
+constexpr int M2L_CHUNK_PAIRS = 16;
 // The FP32 near field runs independent warps, NEAR_WARPS per block, one leaf
 // (up to 64 targets) per work item. The points of N(B) arrive in rounds of at
 // most NEAR_RECS cells and NEAR_CAP point pairs through NEAR_BUFS buffers per
@@ -343,6 +346,7 @@ struct Handle {
     int4 *sym_plan = nullptr;
     float4 *sym_plan_sh = nullptr;
     int64_t n_sym_plan = 0;
+    bool sym_unroll = true;       // symmetric M2L: unrolled pair loop (long staged records) or counted loop
     int4 *sym_items = nullptr;
     int n_sym_items = 0;
     int *sym_item_part = nullptr;
