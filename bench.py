@@ -152,12 +152,16 @@ class ClockSampler:
 
 
 def dist_init(args):
+    """Replicas: one process per GPU (RANK, LOCAL_RANK, WORLD_SIZE from torchrun), joined
+    only for the barrier around the timed region and the slowest rank's time. NCCL on
+    GPUs; gloo where no GPU is visible (the CPU tests of this host logic)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl", init_method="env://")
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo", init_method="env://")
     return ws, rank, local
 
 
@@ -168,13 +172,21 @@ def barrier(ws):
 
 
 def reduce_max(ws, v: float) -> float:
+    """The largest v over the ranks (the slowest replica's time)."""
     if ws == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate(ws: int, units_per_rank: float, steps: int, total_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed in `steps` steps over the
+    slowest rank's time (weak scaling: each replica does the same work)."""
+    return ws * units_per_rank * steps / (total_ms / 1e3)
 
 
 def sample_size(w, n: int) -> int:
@@ -322,7 +334,7 @@ def run_ours(args):
     st_prof = h.stats()
     h.set_profiling(False)
     total_ms = reduce_max(ws, float(sum(step_ms)))
-    value = ws * N * nrhs * args.steps / (total_ms / 1e3)
+    value = aggregate(ws, N * nrhs, args.steps, total_ms)
 
     # FP64 form of the same handle (a few products)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -583,7 +595,7 @@ def run_batch(args):
     step_ms = [a.elapsed_time(c) for a, c in ev]
     total_ms = reduce_max(ws_, sum(step_ms))
     pts = b.points()
-    value = ws_ * pts * args.steps / (total_ms / 1e3)
+    value = aggregate(ws_, pts, args.steps, total_ms)
     # end to end: host inputs copied in, graph replayed, results copied out, every step
     xh = [x.cpu().pin_memory() for x in b.x]
     yh = [torch.empty_like(y, device="cpu").pin_memory() for y in b.y]
