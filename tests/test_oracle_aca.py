@@ -169,3 +169,40 @@ def test_bases_identities(orc, wl, n):
             assert res <= 1e-12 * max(1.0, np.linalg.cond(Ats) * 1e-4)
             checked += 1
     assert checked > 0
+
+
+def test_aca_repeated_row_not_taken(orc):
+    """A row equal to another (two points at one location) is represented by that row
+    exactly: its residual after the other is taken is round-off, and the ACA skips it
+    like a zero row (the smallest unused row is taken next). The copy is never a pivot, the
+    pivot block stays regular, and the crosses approximate the matrix, copy included, as
+    well as those of the matrix without it."""
+    rng = np.random.default_rng(3)
+    X = rng.uniform(0.0, 1.0, (12, 3))
+    Y = rng.uniform(3.0, 4.0, (40, 3))
+    c = orc.Config(d=3, kernel=orc.K_INV_R, kparam=(1.0, 0.0, 0.0, 0.0))
+    A = orc.kernel_block(c, X, Y)
+    B = np.vstack([A, A[4:5]])                      # row 12 repeats row 4
+    for eps in (1e-6, 1e-12):
+        pa, qa, Ua, Va = orc.aca_dense(A, eps)
+        pb, qb, Ub, Vb = orc.aca_dense(B, eps)
+        assert 12 not in pb
+        M = B[np.ix_(pb, qb)]
+        assert np.linalg.cond(M) < 1e12
+        ea = np.linalg.norm(A - Ua @ Va.T) / np.linalg.norm(A)
+        eb = np.linalg.norm(B - Ub @ Vb.T) / np.linalg.norm(B)
+        assert eb <= 10 * eps and ea <= 10 * eps
+
+
+def test_repeated_points_against_dense(orc):
+    """A cloud with repeated points (distinct indices, one location) keeps the product
+    within 10 eps of the dense product; with the repeated rows taken as pivots the pivot
+    blocks were singular and the product was off by orders of magnitude more."""
+    rng = np.random.default_rng(11)
+    P = rng.uniform(0.0, 1.0, (2700, 3))
+    P = np.vstack([P, P[:7], rng.uniform(0.4, 1.4, (600, 3))])
+    x = rng.standard_normal(P.shape[0])
+    c = orc.Config(d=3, leaf_size=32, aca_tol=1e-8, kernel=orc.K_INV_R, kparam=(1.0, 0.0, 0.0, 0.0))
+    h = orc.H2(P, c)
+    y, yd = h.matvec(x), orc.dense_matvec(P, x, c)
+    assert np.linalg.norm(y - yd) <= 10 * 1e-8 * np.linalg.norm(yd)
