@@ -108,8 +108,9 @@ typedef struct {
     double aca_tol;    /* epsilon > 0 of the ACA stopping rule (Eq. 4)            */
     int kernel;        /* NNCA_K_*                                                */
     double kparam[4];  /* [0] scale s, [1] h or a, [2] diagonal value, [3] unused */
-    int symmetric;     /* must be 1: P = Q, K symmetric; uses the shortcut
-                          t^{B,o} = s^{B,i}, s^{B,o} = t^{B,i} (Sec. 5)          */
+    int symmetric;     /* must be 1: K symmetric (K(p, q) = K(q, p)); uses the
+                          shortcut t^{B,o} = s^{B,i}, s^{B,o} = t^{B,i} (Sec. 5),
+                          on P, or on the union [P; Q] for P != Q (nnca_build)   */
     int m2l_form;      /* FP32 M2L of one right-hand side: NNCA_M2L_AUTO the symmetric form
                           where it applies (every f(|p - q|) of an admissible
                           pair evaluated once, for both u_B and u_B'; ranks up
