@@ -2,8 +2,9 @@
  * nnca.h -- C ABI of the GB300 (sm_103a) NNCA H^2 library.
  *
  * Computes the H^2 matrix-vector product y = A x with A(i, j) = K(p_i, p_j)
- * built by the new Nested Cross Approximation (NNCA) of Gujjula &
- * Ambikasaran, "A new Nested Cross Approximation":
+ * (or K(p_i, q_j) for distinct point sets P and Q, see nnca_build) built by
+ * the new Nested Cross Approximation (NNCA) of Gujjula & Ambikasaran, "A new
+ * Nested Cross Approximation":
  *
  *   nnca_build   uniform 2^d tree over the points (Sec. 2.1), neighbour and
  *                interaction lists from the admissibility condition
@@ -27,7 +28,8 @@
  *  - Points: n x d FP64; layout NNCA_LAYOUT_AOS (p[i*d + k]) or
  *    NNCA_LAYOUT_SOA (p[k*n + i]).
  *  - Vectors: nrhs right-hand sides; right-hand side r occupies
- *    x[r*ld + i], i the caller's point index, ld >= n.
+ *    x[r*ld + i], i the caller's point index, ld >= n (for P != Q: x on the
+ *    points of Q, y on those of P, ld >= max(nP, nQ)).
  *  - Streams: `stream` is a cudaStream_t passed as void*; NULL is the legacy
  *    default stream. nnca_build synchronises the stream (it reads sizes back
  *    to the host); nnca_matvec is asynchronous on the stream.
